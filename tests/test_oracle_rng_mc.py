@@ -1,0 +1,147 @@
+"""Pins of the oracle's random numbers and Monte Carlo pricer (Sec. 4)
+against an independent Philox implementation, distribution tests, and the
+closed forms the SABR SDE reduces to (Black, absorbed Bachelier), plus the
+identities every path must satisfy (put-call, martingale)."""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle as O
+from helpers import bachelier_call, black_call
+
+
+# ---------------------------------------------------------------- Philox
+def test_philox_matches_triton_interpreter_implementation():
+    """Triton ships its own Philox4x32-10 (an independent implementation of
+    the published generator); its CPU interpreter runs it without a GPU."""
+    os.environ["TRITON_INTERPRET"] = "1"
+    torch = pytest.importorskip("torch")
+    triton = pytest.importorskip("triton")
+    import triton.language as tl
+
+    @triton.jit
+    def kern(c_ptr, out_ptr, seed, N: tl.constexpr):
+        i = tl.arange(0, N)
+        c0 = tl.load(c_ptr + i * 4 + 0).to(tl.uint32, bitcast=True)
+        c1 = tl.load(c_ptr + i * 4 + 1).to(tl.uint32, bitcast=True)
+        c2 = tl.load(c_ptr + i * 4 + 2).to(tl.uint32, bitcast=True)
+        c3 = tl.load(c_ptr + i * 4 + 3).to(tl.uint32, bitcast=True)
+        a, b, c, d = tl.random.philox(seed, c0, c1, c2, c3)
+        tl.store(out_ptr + i * 4 + 0, a.to(tl.int32, bitcast=True))
+        tl.store(out_ptr + i * 4 + 1, b.to(tl.int32, bitcast=True))
+        tl.store(out_ptr + i * 4 + 2, c.to(tl.int32, bitcast=True))
+        tl.store(out_ptr + i * 4 + 3, d.to(tl.int32, bitcast=True))
+
+    rng = np.random.default_rng(5)
+    N = 64
+    ctr = rng.integers(0, 2 ** 32, size=(N, 4), dtype=np.uint64)
+    ctr[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    seed = int(rng.integers(0, 2 ** 63))
+    c_t = torch.tensor(ctr.astype(np.uint32).view(np.int32).reshape(-1))
+    out = torch.zeros(N * 4, dtype=torch.int32)
+    kern[(1,)](c_t, out, seed, N=N)
+    got = out.numpy().view(np.uint32).reshape(N, 4)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for i in range(N):
+        assert O.philox([int(x) for x in ctr[i]], key) == [int(x) for x in got[i]], i
+
+
+def test_uniform_map_is_exact_in_single_precision_and_open():
+    assert O.u01(0) == 2.0 ** -24
+    assert O.u01(0xFFFFFFFF) == 1.0 - 2.0 ** -24
+    rng = np.random.default_rng(6)
+    for w in rng.integers(0, 2 ** 32, size=2000):
+        u = O.u01(int(w))
+        assert float(np.float32(u)) == u and 0.0 < u < 1.0
+
+
+def _stream(n, key=(123, 456)):
+    w = []
+    for i in range(n):
+        w.extend(O.philox([i, 7, 0, O.TAG_MC], key))
+    return np.array(w, dtype=np.uint64)
+
+
+def test_uniforms_are_uniform_and_normals_normal():
+    w = _stream(8192)
+    u = np.array([O.u01(int(x)) for x in w])
+    counts, _ = np.histogram(u, bins=64, range=(0, 1))
+    assert stats.chisquare(counts).pvalue > 1e-4
+    z = np.array([O.box_muller(u[2 * i], u[2 * i + 1]) for i in range(len(u) // 2)])
+    z1, z2 = z[:, 0], z[:, 1]
+    n = len(z1)
+    for zz in (z1, z2):
+        assert abs(zz.mean()) < 4 / math.sqrt(n)
+        assert abs(zz.var() - 1) < 4 * math.sqrt(2 / n)
+        assert stats.kstest(zz, "norm").pvalue > 1e-4
+    assert abs(np.corrcoef(z1, z2)[0, 1]) < 4 / math.sqrt(n)
+
+
+# ------------------------------------------------------------- time grid
+def test_grid_lands_on_every_maturity():
+    g = O.mc_grid([0.495890], 250.0)
+    assert len(g) == 124 and g[-1] == 0.495890       # ceil(T * 250) steps
+    g = O.mc_grid([1.0, 0.25, 0.5, 0.75], 250.0)
+    assert len(g) == 252 and g[-1] == 1.0  # 0.25 and 0.75 fall between multiples of 1/250
+    g = O.mc_grid([0.1, 0.33], 250.0)
+    assert 0.1 in g and g[-1] == 0.33 and np.all(np.diff(g) > 0) and np.all(np.diff(g) <= 1 / 250 + 1e-15)
+
+
+# ------------------------------------------------------------ MC pricer
+def test_mc_nu0_beta1_is_black():
+    # nu = 0, beta = 1: the forward is a geometric Brownian motion with vol
+    # alpha, which the log-Euler step integrates exactly.
+    T = np.array([0.25, 0.5, 1.0, 1.0, 2.0, 2.0])
+    K = np.array([1.0, 0.9, 1.1, 0.7, 1.0, 1.5])
+    a = 0.3
+    price, se = O.mc_price(O.HAGAN, [a, 1.0, -0.5, 0.0], 1.0, T, K, n_paths=1 << 15,
+                           steps_per_year=50, seed=11, n_threads=4)
+    ref = black_call(1.0, K, T, a)
+    assert np.all(np.abs(price - ref) <= 4 * se), (price - ref) / se
+
+
+def test_mc_beta0_nu0_is_absorbed_bachelier():
+    # beta = 0, nu = 0: dF = alpha dW absorbed at 0; by the reflection
+    # principle a call is worth Bach(f, K) - Bach(-f, K).
+    a, T = 0.4, 1.0
+    K = np.array([0.5, 0.8, 1.0, 1.2, 1.5])
+    price, se = O.mc_price(O.HAGAN, [a, 0.0, 0.0, 0.0], 1.0, np.full(5, T), K,
+                           n_paths=1 << 15, steps_per_year=1000, seed=3, n_threads=4)
+    ref = bachelier_call(1.0, K, T, a) - bachelier_call(-1.0, K, T, a)
+    assert np.all(np.abs(price - ref) <= 4 * se), (price - ref) / se
+
+
+@pytest.mark.parametrize("model,p", [
+    (O.HAGAN, [0.3, 0.5, -0.5, 0.8]),
+    (O.DYN_I, [0.3, 0.7, -0.6, 0.9, 0.5, 1.2]),
+    (O.DYN_II, [0.3, 0.8, -0.5, 0.7, 1.1, 0.6, 0.1, 0.2, 0.25, -0.2]),
+])
+def test_mc_put_call_identity_and_martingale(model, p):
+    T = np.array([0.5, 0.5, 1.0, 1.0, 1.0])
+    K = np.array([0.9, 0.9, 1e-12, 1.2, 1.2])
+    ic = np.array([1, 0, 1, 1, 0], dtype=np.int8)
+    price, se = O.mc_price(model, p, 1.0, T, K, is_call=ic, n_paths=1 << 14,
+                           steps_per_year=250, seed=21, n_threads=4)
+    # K ~ 0 call = E[F_T]: the scheme is a discrete martingale
+    assert abs(price[2] - 1.0) <= 4 * se[2]
+    # pathwise C - P = F_T - K at T = 1
+    assert abs((price[3] - price[4]) - (price[2] - 1.2)) <= 1e-11  # rounding of the path sums
+
+
+def test_mc_discount_and_thread_independence():
+    T = np.array([1.0, 1.0])
+    K = np.array([1.0, 1.1])
+    p1, s1 = O.mc_price(O.HAGAN, [0.3, 0.7, -0.4, 0.6], 1.0, T, K, n_paths=9000, seed=9, n_threads=1)
+    p4, s4 = O.mc_price(O.HAGAN, [0.3, 0.7, -0.4, 0.6], 1.0, T, K, n_paths=9000, seed=9, n_threads=4)
+    assert np.array_equal(p1, p4) and np.array_equal(s1, s4)
+    pd, sd = O.mc_price(O.HAGAN, [0.3, 0.7, -0.4, 0.6], 1.0, T, K, disc=[0.9, 0.5], n_paths=9000, seed=9)
+    np.testing.assert_allclose(pd, p1 * [0.9, 0.5], rtol=1e-15)
+
+
+def test_mc_rejects_infeasible_dynamic_parameters():
+    with pytest.raises(ValueError):
+        O.mc_price(O.DYN_II, [0.3, 0.8, 0.9, 0.7, 0.0, 0.6, 0.3, 0.2, 0.0, 0.0], 1.0, [1.0], [1.0])
