@@ -1,0 +1,222 @@
+/*
+ * sabr.h -- C-ABI of libsabr.so: SABR implied volatilities, Monte Carlo
+ * prices and Simulated-Annealing calibration on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Fernandez, Ferreiro, Garcia, Leitao, Lopez-Salas, Vazquez,
+ * "Static and dynamic SABR stochastic volatility models: calibration and
+ * option pricing using GPUs".  Citations below name the paper's sections and
+ * equation labels.
+ *
+ * Conventions for every entry point
+ *  - Plain C types only; no exceptions cross the ABI.  Every call returns a
+ *    sabr_status; on failure sabr_last_error() gives a message (per thread).
+ *  - "device" pointers are CUDA global-memory pointers of the current device;
+ *    "host" pointers are ordinary (pageable or pinned) host memory.
+ *  - cuda_stream is a cudaStream_t (NULL = legacy default stream).  Calls
+ *    documented as asynchronous only enqueue work on that stream.
+ *  - The caller owns every buffer it passes in; the library never frees
+ *    caller memory.  Library-owned memory lives inside plans and servers and
+ *    is released by their destroy calls.
+ *  - Parameter vector layout, double params[10]:
+ *      [0]=alpha [1]=beta [2]=rho0 [3]=nu0 [4]=a [5]=b
+ *      [6]=d_rho [7]=d_nu [8]=q_rho [9]=q_nu
+ *    Static models (HAGAN, OBLOJ, EXPANDED) read [0..3] (rho = rho0,
+ *    nu = nu0); DYN_I reads [0..5]; DYN_II reads all ten.
+ */
+#ifndef SABR_H
+#define SABR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SABR_OK = 0,
+  SABR_EINVAL = 1,     /* an argument is out of range or inconsistent      */
+  SABR_ENOMEM = 2,     /* device or pinned host memory could not be had    */
+  SABR_ECUDA = 3,      /* a CUDA runtime call failed                       */
+  SABR_ETIMEOUT = 4,   /* a bounded wait ran out                           */
+  SABR_EAGAIN = 5,     /* result not ready yet (server poll)               */
+  SABR_EBUSY = 6,      /* server queue full                                */
+  SABR_ECANCELLED = 7, /* request cancelled before it finished             */
+  SABR_ENOTFOUND = 8   /* unknown server ticket                            */
+} sabr_status;
+
+typedef enum {
+  SABR_HAGAN = 0,    /* Sec. 2.1, eq. (haganf): Hagan implied vol          */
+  SABR_OBLOJ = 1,    /* Sec. 2.1, eq. (sigma-SABR): Oblój correction       */
+  SABR_EXPANDED = 2, /* Sec. 2.1, eq. (vola_SABR): expanded static form    */
+  SABR_DYN_I = 3,    /* Sec. 2.2, eq. (vola_SABRd), eq. (el_fun_1)         */
+  SABR_DYN_II = 4    /* Sec. 2.2, eq. (vola_SABRd), eq. (el_fun_3)         */
+} sabr_model;
+
+typedef enum {
+  SABR_COST_VOL = 0,     /* Technique I (Sec. 5.1): misfit in implied vols */
+  SABR_COST_MC_PRICE = 1 /* Technique II (Sec. 5.2): misfit in MC prices   */
+} sabr_cost;
+
+typedef enum {
+  SABR_FP32 = 0, /* FP32 bulk arithmetic, FP64 misfit sums and re-score */
+  SABR_FP64 = 1  /* FP64 throughout                                     */
+} sabr_precision;
+
+/* ------------------------------------------------------------------------
+ * sabr_implied_vol -- model implied volatility of n European options.
+ * Sec. 2.1 eqs. (haganf), (sigma-SABR), (vola_SABR); Sec. 2.2 eq.
+ * (vola_SABRd) with nu1^2, nu2^2, eta1, eta2^2 of eq. (integrales_SABRd).
+ *   params  host, double[10] (layout above)
+ *   fwd     forward f > 0 common to all n options
+ *   T, K    device, double[n]: maturities (years, > 0) and strikes (> 0)
+ *   vol_out device, double[n]
+ * Asynchronous on cuda_stream.  n == 0 is a no-op.  EINVAL for a bad model,
+ * precision, fwd or parameter set (alpha <= 0, beta outside [0,1], |rho|
+ * >= 1 for static models, nu < 0, a or b < 0).
+ * ------------------------------------------------------------------------ */
+sabr_status sabr_implied_vol(sabr_model model, const double* params,
+                             double fwd, const double* T, const double* K,
+                             int64_t n, double* vol_out,
+                             sabr_precision prec, void* cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * sabr_mc_price -- Monte Carlo prices of n European options on one path
+ * set, Sec. 4: log-Euler scheme eq. (dis_SABRd) (exact lognormal step of
+ * the vol, log-Euler step of the forward with the old vol), price estimator
+ * eq. (payoff).  One path serves every maturity: the step grid is every
+ * multiple of 1/steps_per_year with each maturity inserted.  The forward is
+ * absorbed (frozen at 0) once it falls below 1e-12 * fwd.
+ *   params       host, double[10]; static models use constant nu and rho,
+ *                DYN_I / DYN_II use nu(t), rho(t) at each step's left end
+ *   T, K         host, double[n]; maturities > 0, strikes >= 0
+ *   is_call      host, int8[n] (nonzero = call) or NULL (all calls)
+ *   discount     host, double[n] discount factors or NULL (all 1)
+ *   n_paths      >= 2; path j draws its normals from Philox4x32-10 with
+ *                key = seed and counter (j, step/2, 0, 0x4D430000)
+ *   price_out    device, double[n]
+ *   stderr_out   device, double[n] or NULL: standard error of each price
+ * Asynchronous on cuda_stream; the host arrays are read before return.
+ * Uses library-owned device scratch (per-block partial sums).  EINVAL for
+ * bad sizes, n > 512 options, more than 64 distinct maturities, more than
+ * 8192 time steps, or
+ * parameters violating rho(t) in [-1,1], nu(t) > 0 on (0, max T].
+ * ------------------------------------------------------------------------ */
+sabr_status sabr_mc_price(sabr_model model, const double* params, double fwd,
+                          const double* T, const double* K,
+                          const int8_t* is_call, const double* discount,
+                          int64_t n, int64_t n_paths, double steps_per_year,
+                          uint64_t seed, double* price_out, double* stderr_out,
+                          sabr_precision prec, void* cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Calibration problems (Sec. 3 eqs. (error_calibrate_individual_relativo),
+ * (error_calibrate_relativo); Sec. 5).  All arrays in a problem are HOST
+ * memory and are copied by the call that receives them.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  sabr_model model;
+  sabr_cost cost;
+  sabr_precision prec;
+  double fwd;              /* forward f > 0 shared by all quotes          */
+  int64_t n_quotes;        /* 1 .. 4096                                   */
+  const double* T;         /* [n_quotes] maturities (years) > 0           */
+  const double* K;         /* [n_quotes] strikes > 0                      */
+  const double* market;    /* [n_quotes] market vols (COST_VOL) or prices */
+  const int8_t* is_call;   /* [n_quotes] or NULL: MC cost only            */
+  const double* discount;  /* [n_quotes] or NULL: MC cost only            */
+  int32_t n_chains;        /* SA chains w >= 1                            */
+  int64_t mc_paths;        /* MC cost: paths per evaluation               */
+  double mc_steps_per_year;/* MC cost: 1/dt                               */
+  uint64_t mc_seed;        /* MC cost: Philox key of the common paths     */
+  const double* x0;        /* [10] start point, or NULL = box midpoint    */
+} sabr_problem;
+
+/* Closed box per coordinate; lo[i] == hi[i] fixes coordinate i.  Open
+ * bounds of the paper (alpha > 0, |rho| < 1, nu > 0) are given inset. */
+typedef struct {
+  double lo[10], hi[10];
+} sabr_bounds;
+
+/* Geometric cooling T_k = T0 * factor^k (k = 0 .. n_levels-1); at level k
+ * every chain runs chain_len Metropolis steps with moves
+ * x' = x + s_k (hi - lo) (2u - 1), s_k = max(step_min, step0 sqrt(T_k/T0)).
+ * T0 <= 0 selects T0 = f(x0). */
+typedef struct {
+  double T0;
+  double factor;
+  int32_t n_levels;
+  int32_t chain_len;
+  double step0;
+  double step_min;
+} sabr_cooling;
+
+typedef struct {
+  double params[10];         /* best point seen by any chain            */
+  double misfit;             /* its cost as evaluated in the loop        */
+  double misfit_fp64;        /* its cost re-evaluated in FP64 on the GPU */
+  double restart_params[10]; /* restart point after the last level       */
+  double restart_misfit;
+  int64_t n_evals;           /* cost evaluations (in-box proposals)      */
+  int64_t n_accepts;         /* accepted Metropolis moves                */
+  sabr_status status;
+} sabr_result;
+
+/* ------------------------------------------------------------------------
+ * sabr_calibrate -- Sec. 5, synchronous parallel Simulated Annealing: all
+ * chains start from x0; each runs chain_len Metropolis steps per temperature
+ * level; the lowest final state restarts every chain at the next level.
+ * Proposal uniforms of chain c at (level k, step j) come from Philox4x32-10
+ * with key = seed and counter (c, k, j, 0x53410000 + block).  Out-of-box
+ * (and, for DYN_II, infeasible) proposals are rejected without a cost
+ * evaluation.  Blocking: returns when *out is filled.  Results depend only on
+ * (problem, bounds, cooling, seed), never on batch mix or launch shape.
+ * ------------------------------------------------------------------------ */
+sabr_status sabr_calibrate(const sabr_problem* problem,
+                           const sabr_bounds* bounds,
+                           const sabr_cooling* cooling, uint64_t seed,
+                           sabr_result* out, void* cuda_stream);
+
+/* n independent problems calibrated together in one set of launches;
+ * problems[i] uses bounds[i], cooling[i], seeds[i], out[i].  Blocking. */
+sabr_status sabr_calibrate_batch(int32_t n, const sabr_problem* problems,
+                                 const sabr_bounds* bounds,
+                                 const sabr_cooling* cooling,
+                                 const uint64_t* seeds, sabr_result* out,
+                                 void* cuda_stream);
+
+/* A plan keeps a batch resident in device memory and records its whole
+ * calibration (all levels) as one CUDA graph, so that it can be replayed.
+ * sabr_plan_run is asynchronous; sabr_plan_results waits for the last run
+ * and copies the n results to the host.  use_graph = 0 launches the kernels
+ * one by one instead. */
+typedef struct sabr_plan sabr_plan;
+sabr_status sabr_plan_create(int32_t n, const sabr_problem* problems,
+                             const sabr_bounds* bounds,
+                             const sabr_cooling* cooling,
+                             const uint64_t* seeds, int32_t use_graph,
+                             void* cuda_stream, sabr_plan** out);
+sabr_status sabr_plan_run(sabr_plan* plan, void* cuda_stream);
+sabr_status sabr_plan_results(sabr_plan* plan, sabr_result* out);
+/* Kernel launches one run of the plan enqueues, and the average duration
+ * of its SA level kernels over the last run (ms; 0 if not timed). */
+sabr_status sabr_plan_stats(sabr_plan* plan, int64_t* launches_per_run,
+                            double* level_kernel_ms);
+void sabr_plan_destroy(sabr_plan* plan);
+
+/* Measurement utility (not part of the paper's method): throughput of the
+ * arithmetic pipes on the current device, in operations per SM clock, from
+ * loops of independent operations timed with the SM cycle counter:
+ *   rates[0] FP32 FMA   [1] MUFU ex2   [2] MUFU lg2 (with one FP32 add)
+ *   rates[3] MUFU rsqrt [4] MUFU rcp   [5] MUFU sin  [6] INT32 multiply-add
+ *   rates[7] FP64 FMA
+ * n_rates >= 8.  Blocking; allocates and frees a small device buffer.  The
+ * ALU roofline of the kernels is stated from these rates. */
+sabr_status sabr_probe_pipe_rates(double* rates, int32_t n_rates, void* cuda_stream);
+
+/* Human-readable message of the last failure on this thread. */
+const char* sabr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SABR_H */

@@ -1,0 +1,13 @@
+"""GB300-native (sm_103a) SABR calibration hot path.
+
+Implements the data-parallel core of Fernandez, Ferreiro, Garcia, Leitao,
+Lopez-Salas and Vazquez, "Static and dynamic SABR stochastic volatility
+models: calibration and option pricing using GPUs": implied-vol formulas
+(Sec. 2), Monte Carlo pricing (Sec. 4) and synchronous parallel Simulated
+Annealing calibration (Sec. 5), behind the C-ABI of include/sabr.h.
+"""
+from . import capi  # noqa: F401
+from .capi import (COST_MC_PRICE, COST_VOL, DYN_I, DYN_II, EXPANDED, FP32, FP64, HAGAN,  # noqa: F401
+                   OBLOJ, SabrError)
+from .api import (CalibrationProblem, CalibrationResult, Plan, calibrate, calibrate_batch,  # noqa: F401
+                  implied_vol, mc_price)

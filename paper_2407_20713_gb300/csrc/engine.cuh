@@ -1,0 +1,121 @@
+// engine.cuh -- device-side layout of a batch of calibration problems and
+// the group-collective cost of Sec. 3 eq. (error_calibrate_relativo).
+#pragma once
+#include <cstdint>
+
+#include "../../include/sabr.h"
+#include "sabr_math.cuh"
+
+namespace sabr {
+
+constexpr int kSaBlock = 256;  // threads per SA block
+constexpr int kStateLen = 12;  // restart x[10], restart f, T0
+
+// One problem of a batch, as the kernels see it (all pointers device).
+// Quotes are sorted by maturity; q_* arrays hold the working precision R,
+// q64_* arrays the FP64 values used by the final re-score.
+struct ProblemDev {
+  int model, prec, cost, d;
+  int n_quotes, n_mats, n_chains, n_levels;
+  int chain_len, G, cpb, n_blocks;
+  double fwd, l2f, Tmax;
+  double lo[10], hi[10];
+  double T0_given, step0, step_min;
+  uint32_t key0, key1;
+  const void* q_lfk;   // ln(f/K)
+  const void* q_l2kf;  // log2(K f)
+  const void* q_l2k;   // log2(K)
+  const void* q_T;     // maturity
+  const void* q_w;     // 1/market (FP32) or market (FP64)
+  const int* q_mat;    // maturity index
+  const void* m_T;     // distinct maturities [n_mats]
+  const double* q64_lfk;
+  const double* q64_l2kf;
+  const double* q64_l2k;
+  const double* q64_T;
+  const double* q64_mkt;
+  const double* m64_T;
+  const double* ck;    // factor^k, k < n_levels
+  const double* x0;    // [10]
+  double* state;       // [kStateLen]
+  double* chain_bf;    // [n_chains] best misfit of each chain
+  void* chain_bx;      // [n_chains][10] best point of each chain (R)
+  unsigned long long* chain_ev;
+  unsigned long long* chain_ac;
+  double* part_f;      // [n_blocks] block argmin of the final states
+  int* part_c;
+  double* part_x;      // [n_blocks][10]
+  unsigned int* arrive;
+  sabr_result* result;
+};
+
+// Quote tables of one problem staged in shared memory.
+template <class R> struct SmemQuotes {
+  const R* lfk;
+  const R* l2kf;
+  const R* l2k;
+  const R* T;
+  const R* w;
+  const int* mat;
+  const R* mT;
+};
+
+// ((market - model)/market)^2 term.  FP32 keeps 1/market (one FMA); FP64
+// divides exactly as written.
+__device__ __forceinline__ float resid(float v, float inv_mkt) { return 1.0f - v * inv_mkt; }
+__device__ __forceinline__ double resid(double v, double mkt) { return (mkt - v) / mkt; }
+
+// Cost of point xp evaluated by the G lanes of one chain group.  Lane `lane`
+// takes quotes lane, lane+G, ...; per-lane partial sums are combined by an
+// FP64 xor-butterfly (every lane ends with the same, order-fixed sum).
+// For the dynamic models the lanes first compute the per-maturity polynomial
+// of eq. (vola_SABRd) into `coef` (this group's slice of shared memory).
+template <class R, int MODEL>
+__device__ __forceinline__ double group_cost(const R* xp, int n_quotes, int n_mats, R l2f,
+                                             const SmemQuotes<R>& sq, R* coef, int lane, int G,
+                                             unsigned gmask) {
+  R acc = (R)0;
+  if (MODEL == SABR_HAGAN || MODEL == SABR_OBLOJ) {
+    const StaticConst<R> sc = static_setup<R>(xp);
+    for (int q = lane; q < n_quotes; q += G) {
+      const R v = (MODEL == SABR_HAGAN)
+                      ? vol_hagan<R>(sc, sq.lfk[q], sq.l2kf[q], sq.T[q])
+                      : vol_obloj<R>(sc, sq.lfk[q], sq.l2kf[q], sq.l2k[q], sq.T[q]);
+      const R r = resid(v, sq.w[q]);
+      acc += r * r;
+    }
+  } else if (MODEL == SABR_EXPANDED) {
+    const PolyCoef<R> c0 = expanded_coef<R>(xp, l2f, (R)0);
+    const PolyCoef<R> c1 = expanded_coef<R>(xp, l2f, (R)1);
+    const R bw = c1.c0 - c0.c0;  // B / omega
+    for (int q = lane; q < n_quotes; q += G) {
+      PolyCoef<R> c = c0;
+      c.c0 = c0.c0 + bw * sq.T[q];
+      const R r = resid(vol_poly<R>(c, sq.lfk[q]), sq.w[q]);
+      acc += r * r;
+    }
+  } else {
+    for (int j = lane; j < n_mats; j += G) {
+      const PolyCoef<R> c = dynamic_coef<R, MODEL == SABR_DYN_II>(xp, l2f, sq.mT[j]);
+      coef[3 * j + 0] = c.c0;
+      coef[3 * j + 1] = c.c1;
+      coef[3 * j + 2] = c.c2;
+    }
+    __syncwarp(gmask);
+    for (int q = lane; q < n_quotes; q += G) {
+      const int j = sq.mat[q];
+      PolyCoef<R> c;
+      c.c0 = coef[3 * j + 0];
+      c.c1 = coef[3 * j + 1];
+      c.c2 = coef[3 * j + 2];
+      const R r = resid(vol_poly<R>(c, sq.lfk[q]), sq.w[q]);
+      acc += r * r;
+    }
+    __syncwarp(gmask);
+  }
+  double s = (double)acc;
+  for (int off = G >> 1; off > 0; off >>= 1) s += __shfl_xor_sync(gmask, s, off);
+  return s;
+}
+
+}  // namespace sabr

@@ -1,0 +1,959 @@
+// sa.cu -- synchronous parallel Simulated Annealing (Sec. 5) on the GPU.
+//
+// Work decomposition: a chain is a group of G lanes (G = 1..32, a power of
+// two); lanes split the quotes of the cost function.  A 256-thread block
+// holds 256/G chains of one problem.  One launch of sa_level_kernel runs one
+// temperature level (chain_len Metropolis steps per chain) for every chain of
+// every problem of a launch group; the chains' states live in registers for
+// the whole level.  At the end of the level each block writes the argmin of
+// its chains' final states, and the last block of a problem to finish (an
+// atomic ticket) reduces the block minima in block order and writes the
+// restart point of the next level.  No block ever waits for another.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "common.h"
+#include "engine.cuh"
+
+namespace sabr {
+
+// ---------------------------------------------------------------------------
+// Shared-memory staging of a problem's quotes.
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ SmemQuotes<R> stage_quotes(const ProblemDev& P, unsigned char* base,
+                                                      int nthreads, int tid, unsigned char** end) {
+  const int Q = P.n_quotes, M = P.n_mats;
+  R* lfk = (R*)base;
+  R* l2kf = lfk + Q;
+  R* l2k = l2kf + Q;
+  R* T = l2k + Q;
+  R* w = T + Q;
+  R* mT = w + Q;
+  int* mat = (int*)(mT + M);
+  for (int i = tid; i < Q; i += nthreads) {
+    lfk[i] = ((const R*)P.q_lfk)[i];
+    l2kf[i] = ((const R*)P.q_l2kf)[i];
+    l2k[i] = ((const R*)P.q_l2k)[i];
+    T[i] = ((const R*)P.q_T)[i];
+    w[i] = ((const R*)P.q_w)[i];
+    mat[i] = P.q_mat[i];
+  }
+  for (int j = tid; j < M; j += nthreads) mT[j] = ((const R*)P.m_T)[j];
+  unsigned char* e = (unsigned char*)(mat + Q);
+  *end = (unsigned char*)(((uintptr_t)e + 15) & ~(uintptr_t)15);
+  SmemQuotes<R> sq{lfk, l2kf, l2k, T, w, mat, mT};
+  return sq;
+}
+
+template <int MODEL> struct Dim {
+  static constexpr int value = MODEL == SABR_DYN_II ? 10 : (MODEL == SABR_DYN_I ? 6 : 4);
+};
+
+__device__ __forceinline__ unsigned group_mask(int G) {
+  if (G >= 32) return 0xffffffffu;
+  const int lane32 = threadIdx.x & 31;
+  return ((1u << G) - 1u) << (lane32 & ~(G - 1));
+}
+
+__device__ __forceinline__ void load_problem(const ProblemDev* probs, int pid, ProblemDev* P) {
+  const int words = (int)(sizeof(ProblemDev) / 4);
+  for (int i = threadIdx.x; i < words; i += blockDim.x)
+    ((int*)P)[i] = ((const int*)(probs + pid))[i];
+  __syncthreads();
+}
+
+// Proposal step: x' = x + step (2u - 1).  The FP64 form rounds each
+// operation exactly as written (no contraction into an FMA).
+__device__ __forceinline__ float propose(float x, float step, float u) {
+  return x + step * (2.0f * u - 1.0f);
+}
+__device__ __forceinline__ double propose(double x, double step, double u) {
+  return __dadd_rn(x, __dmul_rn(step, __dsub_rn(__dmul_rn(2.0, u), 1.0)));
+}
+__device__ __forceinline__ bool metropolis(float u, double delta, double Tk) {
+  return u < __expf((float)(-delta / Tk));
+}
+__device__ __forceinline__ bool metropolis(double u, double delta, double Tk) {
+  return u < exp(-delta / Tk);
+}
+
+// ---------------------------------------------------------------------------
+// f(x0) and the restart state of level 0.  One block of G threads per problem.
+// ---------------------------------------------------------------------------
+template <class R, int MODEL>
+__global__ void sa_init_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ plist) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ ProblemDev P;
+  load_problem(probs, plist[blockIdx.x], &P);
+  unsigned char* rest;
+  const SmemQuotes<R> sq = stage_quotes<R>(P, smem, blockDim.x, threadIdx.x, &rest);
+  __syncthreads();
+  R* coef = (R*)rest;
+  const int G = P.G, lane = threadIdx.x;
+  R x[kMaxD];
+#pragma unroll
+  for (int i = 0; i < kMaxD; ++i) x[i] = (R)P.x0[i];
+  double f0 = 0.0;
+  if (lane < G) f0 = group_cost<R, MODEL>(x, P.n_quotes, P.n_mats, (R)P.l2f, sq, coef, lane, G, group_mask(G));
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < kMaxD; ++i) P.state[i] = (double)x[i];
+    P.state[kMaxD] = f0;
+    P.state[kMaxD + 1] = P.T0_given > 0.0 ? P.T0_given : (f0 > 0.0 ? f0 : 1.0);
+    P.result->status = isfinite(f0) ? SABR_OK : SABR_EINVAL;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One temperature level for every chain of a launch group.
+// ---------------------------------------------------------------------------
+template <class R, int MODEL>
+__global__ void __launch_bounds__(kSaBlock) sa_level_kernel(const ProblemDev* __restrict__ probs,
+                                                           const int2* __restrict__ bmap, int level) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ ProblemDev P;
+  const int2 bm = bmap[blockIdx.x];
+  load_problem(probs, bm.x, &P);
+  if (level >= P.n_levels) return;
+
+  unsigned char* rest;
+  const SmemQuotes<R> sq = stage_quotes<R>(P, smem, blockDim.x, threadIdx.x, &rest);
+  constexpr int D = Dim<MODEL>::value;
+  const int G = P.G, cpb = P.cpb;
+  const int g = threadIdx.x / G, lane = threadIdx.x % G;
+  R* coef = (R*)rest + (size_t)g * 3 * P.n_mats;
+  double* red_f = (double*)((R*)rest + (size_t)cpb * 3 * P.n_mats + 16);
+  red_f = (double*)(((uintptr_t)red_f + 15) & ~(uintptr_t)15);
+  R* red_x = (R*)(red_f + cpb);
+  __syncthreads();
+
+  const int chain = bm.y * cpb + g;
+  const bool active = chain < P.n_chains;
+  const unsigned gmask = group_mask(G);
+
+  const double T0 = P.state[kMaxD + 1];
+  const double Tk = __dmul_rn(T0, P.ck[level]);
+  double sk = __dmul_rn(P.step0, __dsqrt_rn(__ddiv_rn(Tk, T0)));
+  if (sk < P.step_min) sk = P.step_min;
+
+  R x[D], bx[D], step[D], lo[D], hi[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    x[i] = (R)P.state[i];
+    step[i] = (R)__dmul_rn(sk, __dsub_rn(P.hi[i], P.lo[i]));
+    lo[i] = (R)P.lo[i];
+    hi[i] = (R)P.hi[i];
+  }
+  double fcur = P.state[kMaxD];
+  double bf = fcur;
+  R* cbx = (R*)P.chain_bx + (size_t)chain * kMaxD;
+  if (active) {
+    if (level == 0) {
+#pragma unroll
+      for (int i = 0; i < D; ++i) bx[i] = x[i];
+    } else {
+      bf = P.chain_bf[chain];
+#pragma unroll
+      for (int i = 0; i < D; ++i) bx[i] = cbx[i];
+    }
+  }
+  unsigned long long ev = 0, ac = 0;
+  const R l2f = (R)P.l2f;
+  const R Tmax = (R)P.Tmax;
+
+  if (active) {
+    for (int st = 0; st < P.chain_len; ++st) {
+      // D move uniforms and one acceptance uniform: words 0..D of Philox
+      // blocks 0, 1, ... with counter (chain, level, step, tag + block).
+      constexpr int NB = (D + 4) / 4;
+      R u[4 * NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const uint4 w = philox4x32_10(
+            make_uint4((uint32_t)chain, (uint32_t)level, (uint32_t)st, kTagSA + (uint32_t)b), P.key0,
+            P.key1);
+        u[4 * b + 0] = u01<R>(w.x);
+        u[4 * b + 1] = u01<R>(w.y);
+        u[4 * b + 2] = u01<R>(w.z);
+        u[4 * b + 3] = u01<R>(w.w);
+      }
+      R xp[D];
+      bool inside = true;
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        xp[i] = propose(x[i], step[i], u[i]);
+        inside = inside && !(xp[i] < lo[i] || xp[i] > hi[i]);
+      }
+      if (MODEL == SABR_DYN_II && inside) inside = case2_feasible<R>(xp, Tmax);
+      if (!inside) continue;
+      const double fp = group_cost<R, MODEL>(xp, P.n_quotes, P.n_mats, l2f, sq, coef, lane, G, gmask);
+      ++ev;
+      if (!(fp == fp)) continue;
+      if (fp < bf) {
+        bf = fp;
+#pragma unroll
+        for (int i = 0; i < D; ++i) bx[i] = xp[i];
+      }
+      const double delta = fp - fcur;
+      if (delta <= 0.0 || metropolis(u[D], delta, Tk)) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) x[i] = xp[i];
+        fcur = fp;
+        ++ac;
+      }
+    }
+    if (lane == 0) {
+      P.chain_bf[chain] = bf;
+#pragma unroll
+      for (int i = 0; i < kMaxD; ++i) cbx[i] = i < D ? bx[i] : (R)0;
+      if (level == 0) {
+        P.chain_ev[chain] = ev;
+        P.chain_ac[chain] = ac;
+      } else {
+        P.chain_ev[chain] += ev;
+        P.chain_ac[chain] += ac;
+      }
+      red_f[g] = fcur;
+#pragma unroll
+      for (int i = 0; i < kMaxD; ++i) red_x[g * kMaxD + i] = i < D ? x[i] : (R)0;
+    }
+  } else if (lane == 0) {
+    red_f[g] = INFINITY;
+  }
+  __syncthreads();
+
+  if (threadIdx.x == 0) {
+    // block argmin of the final states; lowest chain index on a tie
+    int best = 0;
+    double fb = red_f[0];
+    for (int c = 1; c < cpb; ++c)
+      if (red_f[c] < fb) {
+        fb = red_f[c];
+        best = c;
+      }
+    P.part_f[bm.y] = fb;
+    P.part_c[bm.y] = bm.y * cpb + best;
+    for (int i = 0; i < kMaxD; ++i) P.part_x[(size_t)bm.y * kMaxD + i] = (double)red_x[best * kMaxD + i];
+    __threadfence();
+    const unsigned ticket = atomicAdd(P.arrive, 1u);
+    if (ticket == (unsigned)(P.n_blocks - 1)) {
+      // last block of this problem: restart point of the next level
+      __threadfence();
+      int bb = 0;
+      double f = __ldcg(&P.part_f[0]);
+      for (int b = 1; b < P.n_blocks; ++b) {
+        const double v = __ldcg(&P.part_f[b]);
+        if (v < f) {
+          f = v;
+          bb = b;
+        }
+      }
+      for (int i = 0; i < kMaxD; ++i) P.state[i] = __ldcg(&P.part_x[(size_t)bb * kMaxD + i]);
+      P.state[kMaxD] = f;
+      *P.arrive = 0u;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Best point over all chains, FP64 re-score, counters -> result.
+// One 256-thread block per problem.
+// ---------------------------------------------------------------------------
+template <class R, int MODEL>
+__global__ void __launch_bounds__(kSaBlock) sa_finalize_kernel(const ProblemDev* __restrict__ probs,
+                                                              const int* __restrict__ plist) {
+  __shared__ ProblemDev P;
+  __shared__ double s_f[kSaBlock];
+  __shared__ int s_c[kSaBlock];
+  __shared__ unsigned long long s_ev[kSaBlock], s_ac[kSaBlock];
+  __shared__ double s_best[kMaxD];
+  __shared__ double s_coef[3 * kMaxMats];
+  load_problem(probs, plist[blockIdx.x], &P);
+  const int tid = threadIdx.x;
+
+  double fb = INFINITY;
+  int cb = 0x7fffffff;
+  unsigned long long ev = 0, ac = 0;
+  if (P.n_levels > 0) {
+    for (int c = tid; c < P.n_chains; c += blockDim.x) {
+      const double v = P.chain_bf[c];
+      if (v < fb) {
+        fb = v;
+        cb = c;
+      }
+      ev += P.chain_ev[c];
+      ac += P.chain_ac[c];
+    }
+  }
+  s_f[tid] = fb;
+  s_c[tid] = cb;
+  s_ev[tid] = ev;
+  s_ac[tid] = ac;
+  __syncthreads();
+  if (tid == 0) {
+    double f = INFINITY;
+    int c = 0x7fffffff;
+    unsigned long long te = 0, ta = 0;
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      if (s_f[t] < f || (s_f[t] == f && s_c[t] < c)) {
+        f = s_f[t];
+        c = s_c[t];
+      }
+      te += s_ev[t];
+      ta += s_ac[t];
+    }
+    if (P.n_levels == 0 || c == 0x7fffffff) {
+      f = P.state[kMaxD];
+      for (int i = 0; i < kMaxD; ++i) s_best[i] = P.state[i];
+    } else {
+      const R* bx = (const R*)P.chain_bx + (size_t)c * kMaxD;
+      for (int i = 0; i < kMaxD; ++i) s_best[i] = (double)bx[i];
+    }
+    sabr_result* r = P.result;
+    for (int i = 0; i < kMaxD; ++i) {
+      r->params[i] = s_best[i];
+      r->restart_params[i] = P.state[i];
+    }
+    r->misfit = f;
+    r->restart_misfit = P.state[kMaxD];
+    r->n_evals = (int64_t)te;
+    r->n_accepts = (int64_t)ta;
+  }
+  __syncthreads();
+
+  // FP64 re-score of the best point (Sec. 3 eq. error_calibrate_relativo).
+  const double l2f = P.l2f;
+  if (MODEL == SABR_DYN_I || MODEL == SABR_DYN_II) {
+    for (int j = tid; j < P.n_mats; j += blockDim.x) {
+      const PolyCoef<double> c = dynamic_coef<double, MODEL == SABR_DYN_II>(s_best, l2f, P.m64_T[j]);
+      s_coef[3 * j] = c.c0;
+      s_coef[3 * j + 1] = c.c1;
+      s_coef[3 * j + 2] = c.c2;
+    }
+    __syncthreads();
+  }
+  double acc = 0.0;
+  const StaticConst<double> sc = static_setup<double>(s_best);
+  for (int q = tid; q < P.n_quotes; q += blockDim.x) {
+    double v;
+    if (MODEL == SABR_HAGAN) {
+      v = vol_hagan<double>(sc, P.q64_lfk[q], P.q64_l2kf[q], P.q64_T[q]);
+    } else if (MODEL == SABR_OBLOJ) {
+      v = vol_obloj<double>(sc, P.q64_lfk[q], P.q64_l2kf[q], P.q64_l2k[q], P.q64_T[q]);
+    } else if (MODEL == SABR_EXPANDED) {
+      v = vol_poly<double>(expanded_coef<double>(s_best, l2f, P.q64_T[q]), P.q64_lfk[q]);
+    } else {
+      const int j = P.q_mat[q];
+      PolyCoef<double> c;
+      c.c0 = s_coef[3 * j];
+      c.c1 = s_coef[3 * j + 1];
+      c.c2 = s_coef[3 * j + 2];
+      v = vol_poly<double>(c, P.q64_lfk[q]);
+    }
+    const double r = (P.q64_mkt[q] - v) / P.q64_mkt[q];
+    acc += r * r;
+  }
+  __syncthreads();
+  s_f[tid] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0.0;
+    for (int t = 0; t < (int)blockDim.x; ++t) s += s_f[t];
+    P.result->misfit_fp64 = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+namespace {
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Arena {
+  size_t size = 0;
+  size_t take(size_t bytes) {
+    size_t off = align_up(size, 256);
+    size = off + bytes;
+    return off;
+  }
+};
+
+// Host copy of the Case II range test (feasibility of x0).
+void h_range(double c, double q, double k, double d, double Tmax, double& mn, double& mx) {
+  double g0 = c + d, g1 = (c + q * Tmax) * std::exp(-k * Tmax) + d;
+  mn = std::min(g0, g1);
+  mx = std::max(g0, g1);
+  if (k != 0.0 && q != 0.0) {
+    double ts = 1.0 / k - c / q;
+    if (ts > 0.0 && ts < Tmax) {
+      double gs = (c + q * ts) * std::exp(-k * ts) + d;
+      mn = std::min(mn, gs);
+      mx = std::max(mx, gs);
+    }
+  }
+}
+bool h_feasible(int model, const double* x, double Tmax) {
+  if (model != SABR_DYN_II) return true;
+  double rmn, rmx, nmn, nmx;
+  h_range(x[2], x[8], x[4], x[6], Tmax, rmn, rmx);
+  h_range(x[3], x[9], x[5], x[7], Tmax, nmn, nmx);
+  return rmn >= -1.0 && rmx <= 1.0 && nmn > 0.0;
+}
+
+int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+// Lanes per chain: about eight quotes per lane, widened while the whole batch
+// would not fill the GPU (fewer than 64k threads) and quotes remain to split.
+int choose_lanes(int n_quotes, int n_mats, int model, long long batch_chains) {
+  if (const char* e = std::getenv("SABR_LANES")) {
+    int g = std::atoi(e);
+    if (g >= 1 && g <= 32 && (g & (g - 1)) == 0) return g;
+  }
+  int G = next_pow2((n_quotes + 7) / 8);
+  if (model == SABR_DYN_I || model == SABR_DYN_II) G = std::max(G, next_pow2(n_mats));
+  G = std::min(G, 32);
+  const int cap = std::min(32, next_pow2(n_quotes));
+  while (G < cap && batch_chains * G < 65536) G <<= 1;
+  return G;
+}
+
+size_t level_smem_bytes(int prec, int Q, int M, int cpb) {
+  const size_t rs = prec == SABR_FP64 ? 8 : 4;
+  size_t b = (5 * (size_t)Q + M) * rs + 4 * (size_t)Q;
+  b = align_up(b, 16);
+  b += (size_t)cpb * 3 * M * rs + 16 * rs;
+  b = align_up(b, 16) + 16;
+  b += (size_t)cpb * 8 + (size_t)cpb * kMaxD * rs;
+  return align_up(b, 16) + 64;
+}
+
+}  // namespace
+
+struct LaunchGroup {
+  int prec = 0, model = 0;
+  std::vector<int> problems;
+  int total_blocks = 0;
+  int max_levels = 0;
+  size_t smem_level = 0, smem_init = 0;
+  int2* d_bmap = nullptr;
+  int* d_plist = nullptr;
+};
+
+}  // namespace sabr
+
+struct sabr_plan {
+  int device = 0;
+  int n = 0;
+  void* arena = nullptr;
+  sabr::ProblemDev* d_probs = nullptr;
+  sabr_result* d_results = nullptr;
+  sabr_result* h_results = nullptr;
+  std::vector<sabr::LaunchGroup> groups;
+  int max_levels = 0;
+  bool use_graph = false;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t own_stream = nullptr;
+  cudaEvent_t ev_lv0 = nullptr, ev_lv1 = nullptr, ev_done = nullptr;
+  int64_t launches = 0;
+  int64_t level_launches = 0;
+  bool ran = false;
+};
+
+namespace sabr {
+
+template <class R, int MODEL>
+static void set_smem_attr(size_t bytes) {
+  cudaFuncSetAttribute(sa_level_kernel<R, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)bytes);
+  cudaFuncSetAttribute(sa_init_kernel<R, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)bytes);
+}
+
+template <class R>
+static void set_smem_attr_model(int model, size_t bytes) {
+  switch (model) {
+    case SABR_HAGAN: set_smem_attr<R, SABR_HAGAN>(bytes); break;
+    case SABR_OBLOJ: set_smem_attr<R, SABR_OBLOJ>(bytes); break;
+    case SABR_EXPANDED: set_smem_attr<R, SABR_EXPANDED>(bytes); break;
+    case SABR_DYN_I: set_smem_attr<R, SABR_DYN_I>(bytes); break;
+    default: set_smem_attr<R, SABR_DYN_II>(bytes); break;
+  }
+}
+
+template <class R, int MODEL>
+static int64_t enqueue_group(const sabr_plan* p, const LaunchGroup& g, cudaStream_t s, int phase,
+                             int level) {
+  if (phase == 0) {
+    sa_init_kernel<R, MODEL><<<(int)g.problems.size(), 32, g.smem_init, s>>>(p->d_probs, g.d_plist);
+    return 1;
+  }
+  if (phase == 1) {
+    if (level >= g.max_levels) return 0;
+    sa_level_kernel<R, MODEL><<<g.total_blocks, kSaBlock, g.smem_level, s>>>(p->d_probs, g.d_bmap, level);
+    return 1;
+  }
+  sa_finalize_kernel<R, MODEL><<<(int)g.problems.size(), kSaBlock, 0, s>>>(p->d_probs, g.d_plist);
+  return 1;
+}
+
+template <class R>
+static int64_t enqueue_model(const sabr_plan* p, const LaunchGroup& g, cudaStream_t s, int phase, int level) {
+  switch (g.model) {
+    case SABR_HAGAN: return enqueue_group<R, SABR_HAGAN>(p, g, s, phase, level);
+    case SABR_OBLOJ: return enqueue_group<R, SABR_OBLOJ>(p, g, s, phase, level);
+    case SABR_EXPANDED: return enqueue_group<R, SABR_EXPANDED>(p, g, s, phase, level);
+    case SABR_DYN_I: return enqueue_group<R, SABR_DYN_I>(p, g, s, phase, level);
+    default: return enqueue_group<R, SABR_DYN_II>(p, g, s, phase, level);
+  }
+}
+
+// The whole calibration of a plan, enqueued on s.
+static sabr_status enqueue_plan(sabr_plan* p, cudaStream_t s, bool capturing) {
+  int64_t launches = 0, level_launches = 0;
+  for (auto& g : p->groups)
+    launches += g.prec == SABR_FP64 ? enqueue_model<double>(p, g, s, 0, 0) : enqueue_model<float>(p, g, s, 0, 0);
+  if (capturing)
+    SABR_CUDA(cudaEventRecordWithFlags(p->ev_lv0, s, cudaEventRecordExternal));
+  else
+    SABR_CUDA(cudaEventRecord(p->ev_lv0, s));
+  for (int lv = 0; lv < p->max_levels; ++lv)
+    for (auto& g : p->groups) {
+      int64_t k = g.prec == SABR_FP64 ? enqueue_model<double>(p, g, s, 1, lv) : enqueue_model<float>(p, g, s, 1, lv);
+      launches += k;
+      level_launches += k;
+    }
+  if (capturing)
+    SABR_CUDA(cudaEventRecordWithFlags(p->ev_lv1, s, cudaEventRecordExternal));
+  else
+    SABR_CUDA(cudaEventRecord(p->ev_lv1, s));
+  for (auto& g : p->groups)
+    launches += g.prec == SABR_FP64 ? enqueue_model<double>(p, g, s, 2, 0) : enqueue_model<float>(p, g, s, 2, 0);
+  SABR_CUDA(cudaGetLastError());
+  SABR_CUDA(cudaMemcpyAsync(p->h_results, p->d_results, sizeof(sabr_result) * p->n,
+                            cudaMemcpyDeviceToHost, s));
+  p->launches = launches;
+  p->level_launches = level_launches;
+  return SABR_OK;
+}
+
+// Validation and FP64 preprocessing of one problem.
+struct HostProblem {
+  int model, prec, cost, d, n_quotes, n_mats, n_chains, n_levels, chain_len;
+  double fwd, Tmax;
+  std::vector<double> lfk, l2kf, l2k, T, mkt, mT, ck;
+  std::vector<int> mat;
+  double x0[kMaxD];
+  double lo[kMaxD], hi[kMaxD];
+  double T0, step0, step_min;
+  uint64_t seed;
+};
+
+static sabr_status prepare(const sabr_problem& pr, const sabr_bounds& b, const sabr_cooling& c,
+                           uint64_t seed, HostProblem& h) {
+  h.model = pr.model;
+  h.d = n_params(pr.model);
+  if (h.d < 0) return fail(SABR_EINVAL, "unknown model");
+  if (pr.cost != SABR_COST_VOL && pr.cost != SABR_COST_MC_PRICE) return fail(SABR_EINVAL, "unknown cost");
+  if (pr.cost == SABR_COST_MC_PRICE) return fail(SABR_EINVAL, "MC-price cost is calibrated by the MC engine");
+  if (pr.prec != SABR_FP32 && pr.prec != SABR_FP64) return fail(SABR_EINVAL, "unknown precision");
+  if (!(pr.fwd > 0.0) || !std::isfinite(pr.fwd)) return fail(SABR_EINVAL, "fwd must be > 0");
+  if (pr.n_quotes < 1 || pr.n_quotes > kMaxQuotes) return fail(SABR_EINVAL, "n_quotes must lie in [1, 4096]");
+  if (!pr.T || !pr.K || !pr.market) return fail(SABR_EINVAL, "NULL quote array");
+  if (pr.n_chains < 1 || pr.n_chains > (1 << 24)) return fail(SABR_EINVAL, "n_chains must lie in [1, 2^24]");
+  if (!(c.factor > 0.0) || !std::isfinite(c.factor) || c.n_levels < 0 || c.chain_len < 0 ||
+      !(c.step0 >= 0.0) || !(c.step_min >= 0.0) || !std::isfinite(c.T0) || !std::isfinite(c.step0) ||
+      !std::isfinite(c.step_min))
+    return fail(SABR_EINVAL, "bad cooling schedule");
+  h.prec = pr.prec;
+  h.cost = pr.cost;
+  h.n_quotes = (int)pr.n_quotes;
+  h.n_chains = pr.n_chains;
+  h.n_levels = c.n_levels;
+  h.chain_len = c.chain_len;
+  h.fwd = pr.fwd;
+  h.T0 = c.T0;
+  h.step0 = c.step0;
+  h.step_min = c.step_min;
+  h.seed = seed;
+  const int Q = h.n_quotes;
+  std::vector<int> order(Q);
+  for (int i = 0; i < Q; ++i) {
+    if (!(pr.T[i] > 0.0) || !std::isfinite(pr.T[i])) return fail(SABR_EINVAL, "maturities must be > 0");
+    if (!(pr.K[i] > 0.0) || !std::isfinite(pr.K[i])) return fail(SABR_EINVAL, "strikes must be > 0");
+    if (!(pr.market[i] > 0.0) || !std::isfinite(pr.market[i])) return fail(SABR_EINVAL, "market vols must be > 0");
+    order[i] = i;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int bb) { return pr.T[a] < pr.T[bb]; });
+  h.lfk.resize(Q);
+  h.l2kf.resize(Q);
+  h.l2k.resize(Q);
+  h.T.resize(Q);
+  h.mkt.resize(Q);
+  h.mat.resize(Q);
+  h.mT.clear();
+  for (int s = 0; s < Q; ++s) {
+    const int i = order[s];
+    if (h.mT.empty() || pr.T[i] != h.mT.back()) h.mT.push_back(pr.T[i]);
+    h.mat[s] = (int)h.mT.size() - 1;
+    h.lfk[s] = std::log(pr.fwd / pr.K[i]);
+    h.l2kf[s] = std::log2(pr.K[i] * pr.fwd);
+    h.l2k[s] = std::log2(pr.K[i]);
+    h.T[s] = pr.T[i];
+    h.mkt[s] = pr.market[i];
+  }
+  h.n_mats = (int)h.mT.size();
+  if (h.n_mats > kMaxMats) return fail(SABR_EINVAL, "more than 64 distinct maturities");
+  h.Tmax = h.mT.back();
+  for (int i = 0; i < kMaxD; ++i) {
+    h.lo[i] = i < h.d ? b.lo[i] : 0.0;
+    h.hi[i] = i < h.d ? b.hi[i] : 0.0;
+    if (!(h.lo[i] <= h.hi[i]) || !std::isfinite(h.lo[i]) || !std::isfinite(h.hi[i]))
+      return fail(SABR_EINVAL, "bounds need finite lo <= hi");
+    h.x0[i] = i < h.d ? (pr.x0 ? pr.x0[i] : 0.5 * (h.lo[i] + h.hi[i])) : 0.0;
+    if (h.x0[i] < h.lo[i] || h.x0[i] > h.hi[i]) return fail(SABR_EINVAL, "x0 outside the box");
+  }
+  if (!h_feasible(h.model, h.x0, h.Tmax)) return fail(SABR_EINVAL, "x0 violates the Case II constraints");
+  h.ck.resize(std::max(h.n_levels, 1));
+  for (int k = 0; k < h.n_levels; ++k) h.ck[k] = std::pow(c.factor, (double)k);
+  return SABR_OK;
+}
+
+static void free_plan(sabr_plan* p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->ev_lv0) cudaEventDestroy(p->ev_lv0);
+  if (p->ev_lv1) cudaEventDestroy(p->ev_lv1);
+  if (p->ev_done) cudaEventDestroy(p->ev_done);
+  if (p->own_stream) cudaStreamDestroy(p->own_stream);
+  if (p->arena) cudaFree(p->arena);
+  if (p->h_results) cudaFreeHost(p->h_results);
+  delete p;
+}
+
+static sabr_status build_plan(int32_t n, const sabr_problem* problems, const sabr_bounds* bounds,
+                              const sabr_cooling* cooling, const uint64_t* seeds, int use_graph,
+                              cudaStream_t stream, sabr_plan** out) {
+  if (!out) return fail(SABR_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || !problems || !bounds || !cooling || !seeds) return fail(SABR_EINVAL, "empty batch or NULL array");
+  std::vector<HostProblem> hp(n);
+  long long batch_chains = 0;
+  for (int i = 0; i < n; ++i) {
+    SABR_TRY(prepare(problems[i], bounds[i], cooling[i], seeds[i], hp[i]));
+    batch_chains += hp[i].n_chains;
+  }
+  sabr_plan* p = new sabr_plan();
+  p->n = n;
+  cudaGetDevice(&p->device);
+
+  // Arena layout.
+  Arena ar;
+  struct Off {
+    size_t lfk, l2kf, l2k, T, w, mat, mT, q64_lfk, q64_l2kf, q64_l2k, q64_T, q64_mkt, m64_T, ck, x0, state,
+        bf, bx, ev, ac, pf, pc, px, arrive;
+  };
+  std::vector<Off> off(n);
+  std::vector<ProblemDev> pd(n);
+  size_t probs_off = ar.take(sizeof(ProblemDev) * n);
+  size_t results_off = ar.take(sizeof(sabr_result) * n);
+  for (int i = 0; i < n; ++i) {
+    HostProblem& h = hp[i];
+    ProblemDev& d = pd[i];
+    std::memset(&d, 0, sizeof(d));
+    d.model = h.model;
+    d.prec = h.prec;
+    d.cost = h.cost;
+    d.d = h.d;
+    d.n_quotes = h.n_quotes;
+    d.n_mats = h.n_mats;
+    d.n_chains = h.n_chains;
+    d.n_levels = h.n_levels;
+    d.chain_len = h.chain_len;
+    d.G = choose_lanes(h.n_quotes, h.n_mats, h.model, batch_chains);
+    d.cpb = kSaBlock / d.G;
+    d.n_blocks = (h.n_chains + d.cpb - 1) / d.cpb;
+    d.fwd = h.fwd;
+    d.l2f = std::log2(h.fwd);
+    d.Tmax = h.Tmax;
+    for (int k = 0; k < kMaxD; ++k) {
+      d.lo[k] = h.lo[k];
+      d.hi[k] = h.hi[k];
+    }
+    d.T0_given = h.T0;
+    d.step0 = h.step0;
+    d.step_min = h.step_min;
+    d.key0 = (uint32_t)h.seed;
+    d.key1 = (uint32_t)(h.seed >> 32);
+    const size_t rs = h.prec == SABR_FP64 ? 8 : 4;
+    const size_t Q = h.n_quotes, M = h.n_mats;
+    Off& o = off[i];
+    o.lfk = ar.take(Q * rs);
+    o.l2kf = ar.take(Q * rs);
+    o.l2k = ar.take(Q * rs);
+    o.T = ar.take(Q * rs);
+    o.w = ar.take(Q * rs);
+    o.mat = ar.take(Q * 4);
+    o.mT = ar.take(M * rs);
+    o.q64_lfk = ar.take(Q * 8);
+    o.q64_l2kf = ar.take(Q * 8);
+    o.q64_l2k = ar.take(Q * 8);
+    o.q64_T = ar.take(Q * 8);
+    o.q64_mkt = ar.take(Q * 8);
+    o.m64_T = ar.take(M * 8);
+    o.ck = ar.take(h.ck.size() * 8);
+    o.x0 = ar.take(kMaxD * 8);
+    o.state = ar.take(kStateLen * 8);
+    o.bf = ar.take((size_t)h.n_chains * 8);
+    o.bx = ar.take((size_t)h.n_chains * kMaxD * rs);
+    o.ev = ar.take((size_t)h.n_chains * 8);
+    o.ac = ar.take((size_t)h.n_chains * 8);
+    o.pf = ar.take((size_t)d.n_blocks * 8);
+    o.pc = ar.take((size_t)d.n_blocks * 4);
+    o.px = ar.take((size_t)d.n_blocks * kMaxD * 8);
+    o.arrive = ar.take(4);
+  }
+  // launch groups: one per (precision, model)
+  for (int i = 0; i < n; ++i) {
+    LaunchGroup* g = nullptr;
+    for (auto& gg : p->groups)
+      if (gg.prec == hp[i].prec && gg.model == hp[i].model) g = &gg;
+    if (!g) {
+      p->groups.push_back(LaunchGroup());
+      g = &p->groups.back();
+      g->prec = hp[i].prec;
+      g->model = hp[i].model;
+    }
+    g->problems.push_back(i);
+    g->total_blocks += pd[i].n_blocks;
+    g->max_levels = std::max(g->max_levels, hp[i].n_levels);
+    g->smem_level = std::max(g->smem_level, level_smem_bytes(hp[i].prec, hp[i].n_quotes, hp[i].n_mats, pd[i].cpb));
+    g->smem_init = std::max(g->smem_init, level_smem_bytes(hp[i].prec, hp[i].n_quotes, hp[i].n_mats, 1));
+    p->max_levels = std::max(p->max_levels, hp[i].n_levels);
+  }
+  std::vector<size_t> bmap_off(p->groups.size()), plist_off(p->groups.size());
+  for (size_t gi = 0; gi < p->groups.size(); ++gi) {
+    bmap_off[gi] = ar.take(sizeof(int2) * p->groups[gi].total_blocks);
+    plist_off[gi] = ar.take(sizeof(int) * p->groups[gi].problems.size());
+  }
+
+  // Host image of the arena, then one copy.
+  std::vector<unsigned char> img(ar.size, 0);
+  cudaError_t e = cudaMalloc(&p->arena, ar.size);
+  if (e != cudaSuccess) {
+    free_plan(p);
+    return cuda_fail(e, "cudaMalloc(plan arena)");
+  }
+  unsigned char* base = (unsigned char*)p->arena;
+  auto put = [&](size_t o, const void* src, size_t bytes) { std::memcpy(img.data() + o, src, bytes); };
+  for (int i = 0; i < n; ++i) {
+    HostProblem& h = hp[i];
+    ProblemDev& d = pd[i];
+    Off& o = off[i];
+    const int Q = h.n_quotes, M = h.n_mats;
+    if (h.prec == SABR_FP64) {
+      put(o.lfk, h.lfk.data(), Q * 8);
+      put(o.l2kf, h.l2kf.data(), Q * 8);
+      put(o.l2k, h.l2k.data(), Q * 8);
+      put(o.T, h.T.data(), Q * 8);
+      put(o.w, h.mkt.data(), Q * 8);
+      put(o.mT, h.mT.data(), M * 8);
+    } else {
+      std::vector<float> t(Q);
+      for (int k = 0; k < Q; ++k) t[k] = (float)h.lfk[k];
+      put(o.lfk, t.data(), Q * 4);
+      for (int k = 0; k < Q; ++k) t[k] = (float)h.l2kf[k];
+      put(o.l2kf, t.data(), Q * 4);
+      for (int k = 0; k < Q; ++k) t[k] = (float)h.l2k[k];
+      put(o.l2k, t.data(), Q * 4);
+      for (int k = 0; k < Q; ++k) t[k] = (float)h.T[k];
+      put(o.T, t.data(), Q * 4);
+      for (int k = 0; k < Q; ++k) t[k] = (float)(1.0 / h.mkt[k]);
+      put(o.w, t.data(), Q * 4);
+      std::vector<float> tm(M);
+      for (int k = 0; k < M; ++k) tm[k] = (float)h.mT[k];
+      put(o.mT, tm.data(), M * 4);
+    }
+    put(o.mat, h.mat.data(), Q * 4);
+    put(o.q64_lfk, h.lfk.data(), Q * 8);
+    put(o.q64_l2kf, h.l2kf.data(), Q * 8);
+    put(o.q64_l2k, h.l2k.data(), Q * 8);
+    put(o.q64_T, h.T.data(), Q * 8);
+    put(o.q64_mkt, h.mkt.data(), Q * 8);
+    put(o.m64_T, h.mT.data(), M * 8);
+    put(o.ck, h.ck.data(), h.ck.size() * 8);
+    put(o.x0, h.x0, kMaxD * 8);
+    d.q_lfk = base + o.lfk;
+    d.q_l2kf = base + o.l2kf;
+    d.q_l2k = base + o.l2k;
+    d.q_T = base + o.T;
+    d.q_w = base + o.w;
+    d.q_mat = (const int*)(base + o.mat);
+    d.m_T = base + o.mT;
+    d.q64_lfk = (const double*)(base + o.q64_lfk);
+    d.q64_l2kf = (const double*)(base + o.q64_l2kf);
+    d.q64_l2k = (const double*)(base + o.q64_l2k);
+    d.q64_T = (const double*)(base + o.q64_T);
+    d.q64_mkt = (const double*)(base + o.q64_mkt);
+    d.m64_T = (const double*)(base + o.m64_T);
+    d.ck = (const double*)(base + o.ck);
+    d.x0 = (const double*)(base + o.x0);
+    d.state = (double*)(base + o.state);
+    d.chain_bf = (double*)(base + o.bf);
+    d.chain_bx = base + o.bx;
+    d.chain_ev = (unsigned long long*)(base + o.ev);
+    d.chain_ac = (unsigned long long*)(base + o.ac);
+    d.part_f = (double*)(base + o.pf);
+    d.part_c = (int*)(base + o.pc);
+    d.part_x = (double*)(base + o.px);
+    d.arrive = (unsigned int*)(base + o.arrive);
+    d.result = (sabr_result*)(base + results_off) + i;
+  }
+  put(probs_off, pd.data(), sizeof(ProblemDev) * n);
+  for (size_t gi = 0; gi < p->groups.size(); ++gi) {
+    LaunchGroup& g = p->groups[gi];
+    std::vector<int2> bm;
+    for (int pi : g.problems)
+      for (int b = 0; b < pd[pi].n_blocks; ++b) bm.push_back(make_int2(pi, b));
+    put(bmap_off[gi], bm.data(), sizeof(int2) * bm.size());
+    put(plist_off[gi], g.problems.data(), sizeof(int) * g.problems.size());
+    g.d_bmap = (int2*)(base + bmap_off[gi]);
+    g.d_plist = (int*)(base + plist_off[gi]);
+    if (g.prec == SABR_FP64)
+      set_smem_attr_model<double>(g.model, std::max(g.smem_level, g.smem_init));
+    else
+      set_smem_attr_model<float>(g.model, std::max(g.smem_level, g.smem_init));
+  }
+  p->d_probs = (ProblemDev*)(base + probs_off);
+  p->d_results = (sabr_result*)(base + results_off);
+  e = cudaMemcpy(p->arena, img.data(), ar.size, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMallocHost(&p->h_results, sizeof(sabr_result) * n);
+  if (e == cudaSuccess) e = cudaEventCreate(&p->ev_lv0);
+  if (e == cudaSuccess) e = cudaEventCreate(&p->ev_lv1);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_done, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    free_plan(p);
+    return cuda_fail(e, "plan set-up");
+  }
+  p->use_graph = use_graph != 0;
+  if (p->use_graph) {
+    cudaStream_t cs = stream;
+    if (!cs) {
+      e = cudaStreamCreateWithFlags(&p->own_stream, cudaStreamNonBlocking);
+      if (e != cudaSuccess) {
+        free_plan(p);
+        return cuda_fail(e, "cudaStreamCreate");
+      }
+      cs = p->own_stream;
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      free_plan(p);
+      return cuda_fail(e, "cudaStreamBeginCapture");
+    }
+    sabr_status st = enqueue_plan(p, cs, true);
+    e = cudaStreamEndCapture(cs, &graph);
+    if (st != SABR_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      free_plan(p);
+      return st != SABR_OK ? st : cuda_fail(e, "cudaStreamEndCapture");
+    }
+    e = cudaGraphInstantiate(&p->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      free_plan(p);
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+  }
+  *out = p;
+  return SABR_OK;
+}
+
+static sabr_status run_plan(sabr_plan* p, cudaStream_t s) {
+  if (p->use_graph) {
+    SABR_CUDA(cudaGraphLaunch(p->exec, s));
+  } else {
+    SABR_TRY(enqueue_plan(p, s, false));
+  }
+  SABR_CUDA(cudaEventRecord(p->ev_done, s));
+  p->ran = true;
+  return SABR_OK;
+}
+
+static sabr_status plan_results(sabr_plan* p, sabr_result* out) {
+  if (!p->ran) return fail(SABR_EINVAL, "plan has not been run");
+  SABR_CUDA(cudaEventSynchronize(p->ev_done));
+  std::memcpy(out, p->h_results, sizeof(sabr_result) * p->n);
+  return SABR_OK;
+}
+
+}  // namespace sabr
+
+extern "C" {
+
+sabr_status sabr_plan_create(int32_t n, const sabr_problem* problems, const sabr_bounds* bounds,
+                             const sabr_cooling* cooling, const uint64_t* seeds, int32_t use_graph,
+                             void* stream, sabr_plan** out) {
+  sabr::clear_error();
+  return sabr::build_plan(n, problems, bounds, cooling, seeds, use_graph, (cudaStream_t)stream, out);
+}
+
+sabr_status sabr_plan_run(sabr_plan* plan, void* stream) {
+  sabr::clear_error();
+  if (!plan) return sabr::fail(SABR_EINVAL, "plan is NULL");
+  return sabr::run_plan(plan, (cudaStream_t)stream);
+}
+
+sabr_status sabr_plan_results(sabr_plan* plan, sabr_result* out) {
+  sabr::clear_error();
+  if (!plan || !out) return sabr::fail(SABR_EINVAL, "NULL argument");
+  return sabr::plan_results(plan, out);
+}
+
+sabr_status sabr_plan_stats(sabr_plan* plan, int64_t* launches, double* level_ms) {
+  sabr::clear_error();
+  if (!plan) return sabr::fail(SABR_EINVAL, "plan is NULL");
+  if (launches) *launches = plan->launches;
+  if (level_ms) {
+    *level_ms = 0.0;
+    if (plan->ran && plan->level_launches > 0) {
+      SABR_CUDA(cudaEventSynchronize(plan->ev_done));
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, plan->ev_lv0, plan->ev_lv1) == cudaSuccess)
+        *level_ms = (double)ms / (double)plan->level_launches;
+    }
+  }
+  return SABR_OK;
+}
+
+void sabr_plan_destroy(sabr_plan* plan) { sabr::free_plan(plan); }
+
+sabr_status sabr_calibrate_batch(int32_t n, const sabr_problem* problems, const sabr_bounds* bounds,
+                                 const sabr_cooling* cooling, const uint64_t* seeds, sabr_result* out,
+                                 void* stream) {
+  sabr::clear_error();
+  if (!out) return sabr::fail(SABR_EINVAL, "out is NULL");
+  sabr_plan* p = nullptr;
+  SABR_TRY(sabr::build_plan(n, problems, bounds, cooling, seeds, 0, (cudaStream_t)stream, &p));
+  sabr_status st = sabr::run_plan(p, (cudaStream_t)stream);
+  if (st == SABR_OK) st = sabr::plan_results(p, out);
+  sabr::free_plan(p);
+  return st;
+}
+
+sabr_status sabr_calibrate(const sabr_problem* problem, const sabr_bounds* bounds,
+                           const sabr_cooling* cooling, uint64_t seed, sabr_result* out, void* stream) {
+  return sabr_calibrate_batch(1, problem, bounds, cooling, &seed, out, stream);
+}
+
+}  // extern "C"

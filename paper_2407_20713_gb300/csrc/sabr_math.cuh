@@ -1,0 +1,487 @@
+// sabr_math.cuh -- device arithmetic of the SABR hot path, templated on the
+// working precision R (float = FP32 bulk, double = FP64 form).
+//
+//  * Philox4x32-10 counter-based generator and the (0,1) uniform map.
+//  * z/x(z) of Sec. 2.1 eq. (equis) in a cancellation-free form.
+//  * Static implied vols: eq. (haganf), eq. (sigma-SABR), eq. (vola_SABR).
+//  * Dynamic coefficients nu1^2, nu2^2, eta1, eta2^2 of Sec. 2.2
+//    eq. (integrales_SABRd) for Case I (eq. el_fun_1) and Case II
+//    (eq. el_fun_3), and the per-maturity polynomial of eq. (vola_SABRd).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sabr {
+
+// ---------------------------------------------------------------------------
+// Precision traits
+// ---------------------------------------------------------------------------
+template <class R> struct Tr;
+template <> struct Tr<float> {
+  static constexpr int kSeries = 20;   // series terms for |arg| < 2 or 5
+  static constexpr int kGauss = 8;     // Gauss-Legendre nodes per panel
+};
+template <> struct Tr<double> {
+  static constexpr int kSeries = 32;
+  static constexpr int kGauss = 16;
+};
+
+__device__ __forceinline__ float m_exp(float x) { return expf(x); }
+__device__ __forceinline__ double m_exp(double x) { return exp(x); }
+__device__ __forceinline__ float m_exp2(float x) { return exp2f(x); }
+__device__ __forceinline__ double m_exp2(double x) { return exp2(x); }
+__device__ __forceinline__ float m_log(float x) { return logf(x); }
+__device__ __forceinline__ double m_log(double x) { return log(x); }
+__device__ __forceinline__ float m_log2(float x) { return log2f(x); }
+__device__ __forceinline__ double m_log2(double x) { return log2(x); }
+__device__ __forceinline__ float m_log1p(float x) { return log1pf(x); }
+__device__ __forceinline__ double m_log1p(double x) { return log1p(x); }
+__device__ __forceinline__ float m_expm1(float x) { return expm1f(x); }
+__device__ __forceinline__ double m_expm1(double x) { return expm1(x); }
+__device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
+
+// ---------------------------------------------------------------------------
+// Compile-time tables: factorials and Gauss-Legendre rules (nodes found by
+// Newton's method on P_n from cosine initial guesses, all constexpr).
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr double cx_fact(int n) {
+  double f = 1.0;
+  for (int i = 2; i <= n; ++i) f *= i;
+  return f;
+}
+__host__ __device__ constexpr double cx_cos(double x) {
+  double term = 1.0, sum = 1.0;
+  for (int k = 1; k < 40; ++k) {
+    term *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
+    sum += term;
+  }
+  return sum;
+}
+template <int N> struct GaussRule {
+  double x[N], w[N];  // nodes/weights on [-1, 1]
+};
+template <int N> __host__ __device__ constexpr GaussRule<N> make_gauss() {
+  GaussRule<N> g{};
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < N; ++i) {
+    double x = cx_cos(pi * (i + 0.75) / (N + 0.5));
+    double p = 0, dp = 1;
+    for (int it = 0; it < 60; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int k = 1; k < N; ++k) {
+        double p2 = ((2.0 * k + 1.0) * x * p1 - k * p0) / (k + 1.0);
+        p0 = p1;
+        p1 = p2;
+      }
+      p = p1;
+      dp = N * (x * p1 - p0) / (x * x - 1.0);
+      x -= p / dp;
+    }
+    double p0 = 1.0, p1 = x;
+    for (int k = 1; k < N; ++k) {
+      double p2 = ((2.0 * k + 1.0) * x * p1 - k * p0) / (k + 1.0);
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = N * (x * p1 - p0) / (x * x - 1.0);
+    g.x[i] = x;
+    g.w[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+  return g;
+}
+// Device copies of the rules, constant-initialised at compile time.
+template <int N> __constant__ GaussRule<N> kGaussRule = make_gauss<N>();
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64
+// multiplications, key bumped by the golden-ratio Weyl constants.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t ma = 0xD2511F53u, mb = 0xCD9E8D57u;
+    const uint32_t ha = __umulhi(ma, c.x), la = ma * c.x;
+    const uint32_t hb = __umulhi(mb, c.z), lb = mb * c.z;
+    c = make_uint4(hb ^ c.y ^ k0, lb, ha ^ c.w ^ k1, la);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+constexpr uint32_t kTagSA = 0x53410000u;
+constexpr uint32_t kTagMC = 0x4D430000u;
+
+// 23 random bits + 1/2, scaled by 2^-23: exact in float, strictly in (0,1).
+template <class R> __device__ __forceinline__ R u01(uint32_t w) {
+  return ((R)(w >> 9) + (R)0.5) * (R)1.1920928955078125e-07;
+}
+
+// ---------------------------------------------------------------------------
+// z / x(z), eq. (equis):  x = ln((D + z - rho)/(1 - rho)),
+// D = sqrt(1 - 2 rho z + z^2) = sqrt((z - rho)^2 + (1 - rho)(1 + rho)).
+// Writing u for the log's argument, u - 1 = 2 z / (1 - z + D) exactly, whose
+// denominator is a sum of positive terms when z < 1; there x = log1p(u - 1)
+// unless u < 1/2, where u = (1 + rho) / (D - (z - rho)) is formed directly.
+// For z >= 1 the printed form has no cancellation.  omr = 1 - rho and
+// opr = 1 + rho are passed in, formed from the FP64 parameter.
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ R z_over_x(R z, R rho, R omr, R opr) {
+  if (z == (R)0) return (R)1;
+  const R zr = z - rho;
+  const R D = m_sqrt(zr * zr + omr * opr);
+  R x;
+  if (z < (R)1) {
+    const R w = (R)2 * z / ((R)1 - z + D);
+    x = (w >= (R)-0.5) ? m_log1p(w) : m_log(opr / (D - zr));
+  } else {
+    x = m_log((D + zr) / omr);
+  }
+  return z / x;
+}
+
+// ---------------------------------------------------------------------------
+// Per-quote inputs (parameter independent, formed in FP64 on the host):
+//   lfk  = ln(f/K)        l2kf = log2(K f)       l2k = log2(K)      T
+// ---------------------------------------------------------------------------
+template <class R> struct StaticConst {
+  R alpha, beta, rho, nu;
+  R omb, half_omb, c2, c4, nu_over_alpha, br_a, br_b, br_c, omr, opr;
+};
+
+// params: x[0..3] = alpha, beta, rho, nu (any real type)
+template <class R, class P>
+__device__ __forceinline__ StaticConst<R> static_setup(const P* x) {
+  StaticConst<R> s;
+  s.alpha = (R)x[0];
+  s.beta = (R)x[1];
+  s.rho = (R)x[2];
+  s.nu = (R)x[3];
+  s.omb = (R)1 - s.beta;
+  s.half_omb = (R)0.5 * s.omb;
+  s.c2 = s.omb * s.omb / (R)24;
+  s.c4 = s.omb * s.omb * s.omb * s.omb / (R)1920;
+  s.nu_over_alpha = s.nu / s.alpha;
+  s.br_a = s.c2 * s.alpha * s.alpha;
+  s.br_b = (R)0.25 * s.rho * s.beta * s.nu * s.alpha;
+  s.br_c = ((R)2 - (R)3 * s.rho * s.rho) / (R)24 * s.nu * s.nu;
+  s.omr = (R)1 - s.rho;
+  s.opr = (R)1 + s.rho;
+  return s;
+}
+
+// eq. (haganf) with z of eq. (zeta); (K f)^{+-(1-beta)/2} from log2(K f).
+template <class R>
+__device__ __forceinline__ R vol_hagan(const StaticConst<R>& s, R lfk, R l2kf, R T) {
+  const R e = s.half_omb * l2kf;
+  const R fk = m_exp2(e), fkinv = m_exp2(-e);
+  const R L2 = lfk * lfk;
+  const R den = (R)1 + L2 * (s.c2 + s.c4 * L2);
+  const R z = s.nu_over_alpha * fk * lfk;
+  const R zx = z_over_x<R>(z, s.rho, s.omr, s.opr);
+  const R brk = (R)1 + (s.br_a * fkinv * fkinv + s.br_b * fkinv + s.br_c) * T;
+  return s.alpha * fkinv * zx * brk / den;
+}
+
+// eq. (sigma-SABR): z = nu (f^{1-b} - K^{1-b}) / (alpha (1-b)); the
+// difference is K^{1-b} expm1((1-b) ln(f/K)), its b -> 1 limit ln(f/K);
+// nu ln(f/K)/x(z) = (alpha ln(f/K)/zd) (z/x(z)), alpha/K^{1-b} at K = f.
+template <class R>
+__device__ __forceinline__ R vol_obloj(const StaticConst<R>& s, R lfk, R l2kf, R l2k, R T) {
+  const R kpow = m_exp2(s.omb * l2k);  // K^{1-beta}
+  const R zd = (s.omb == (R)0) ? lfk : kpow * m_expm1(s.omb * lfk) / s.omb;
+  const R z = s.nu * zd / s.alpha;
+  const R lead = (lfk == (R)0) ? s.alpha / kpow : s.alpha * lfk / zd;
+  const R fkinv = m_exp2(-s.half_omb * l2kf);
+  const R L2 = lfk * lfk;
+  const R den = (R)1 + L2 * (s.c2 + s.c4 * L2);
+  const R brk = (R)1 + (s.br_a * fkinv * fkinv + s.br_b * fkinv + s.br_c) * T;
+  return lead * z_over_x<R>(z, s.rho, s.omr, s.opr) * brk / den;
+}
+
+// ---------------------------------------------------------------------------
+// Polynomial form sigma = c0 + c1 L + c2 L^2 with L = ln(K/f) = -lfk, used
+// by eq. (vola_SABR) (c0 carries B T) and by eq. (vola_SABRd) per maturity.
+// ---------------------------------------------------------------------------
+template <class R> struct PolyCoef {
+  R c0, c1, c2;
+};
+
+// eq. (vola_SABR): omega = f^{1-beta}/alpha (log2 f given).
+template <class R, class P>
+__device__ __forceinline__ PolyCoef<R> expanded_coef(const P* x, R l2f, R T) {
+  const R alpha = (R)x[0], beta = (R)x[1], rho = (R)x[2], nu = (R)x[3];
+  const R omb = (R)1 - beta;
+  const R w = m_exp2(omb * l2f) / alpha;
+  const R rnw = rho * nu * w;
+  const R A1 = (R)-0.5 * (omb - rnw);
+  const R A2 = (omb * omb + (R)3 * (omb - rnw) + ((R)2 - (R)3 * rho * rho) * nu * nu * w * w) / (R)12;
+  const R B = omb * omb / ((R)24 * w * w) + beta * rho * nu / ((R)4 * w) +
+              ((R)2 - (R)3 * rho * rho) / (R)24 * nu * nu;
+  PolyCoef<R> c;
+  c.c0 = ((R)1 + B * T) / w;
+  c.c1 = A1 / w;
+  c.c2 = A2 / w;
+  return c;
+}
+
+// eq. (vola_SABRd) from the four functions at T.
+template <class R>
+__device__ __forceinline__ PolyCoef<R> dynamic_poly(R alpha, R beta, R l2f, R T, R nu1sq,
+                                                    R nu2sq, R eta1, R eta2sq) {
+  const R omb = (R)1 - beta;
+  const R w = m_exp2(omb * l2f) / alpha;
+  const R A1 = (beta - (R)1) / (R)2 + eta1 * w / (R)2;
+  const R A2 = omb * omb / (R)12 + (omb - eta1 * w) / (R)4 +
+               ((R)4 * nu1sq + (R)3 * (eta2sq - (R)3 * eta1 * eta1)) / (R)24 * w * w;
+  const R B = (omb * omb / (R)24 + w * beta * eta1 / (R)4 +
+               ((R)2 * nu2sq - (R)3 * eta2sq) / (R)24 * w * w) / (w * w);
+  PolyCoef<R> c;
+  c.c0 = ((R)1 + B * T) / w;
+  c.c1 = A1 / w;
+  c.c2 = A2 / w;
+  return c;
+}
+
+template <class R>
+__device__ __forceinline__ R vol_poly(const PolyCoef<R>& c, R lfk) {
+  const R L = -lfk;
+  return c.c0 + L * (c.c1 + L * c.c2);
+}
+
+// ---------------------------------------------------------------------------
+// Case I, eq. (exact-integral-expressions), each function written as
+// (constant) x g(argument) with g evaluated by its Taylor series for
+// argument < 2 (where the printed closed forms cancel) and by the closed form
+// otherwise:
+//   nu1^2 = 6 nu0^2 g1(2bT),  g1(x) = (x^2/2 - x + 1 - e^-x)/x^3
+//         = sum_{k>=0} (-x)^k / (k+3)!
+//   nu2^2 = 6 nu0^2 g2(2bT),  g2(x) = (2(e^-x - 1) + x(e^-x + 1))/x^3
+//         = sum_{k>=0} (-x)^k (k+1)/(k+3)!
+//   eta1  = 2 nu0 rho0 g3(y), g3(y) = (e^-y - 1 + y)/y^2
+//         = sum_{k>=0} (-y)^k / (k+2)!,            y = (a+b)T
+//   eta2^2 = 3 nu0^2 rho0^2 g4(y),
+//         g4(y) = (e^-2y - 8 e^-y + 7 + 2y(y-3))/y^4
+//         = sum_{k>=0} (-y)^k (2^{k+4} - 8)/(k+4)!
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr double g1c(int k) { return 1.0 / cx_fact(k + 3); }
+__host__ __device__ constexpr double g2c(int k) { return (k + 1.0) / cx_fact(k + 3); }
+__host__ __device__ constexpr double g3c(int k) { return 1.0 / cx_fact(k + 2); }
+__host__ __device__ constexpr double g4c(int k) {
+  double p = 1.0;
+  for (int i = 0; i < k + 4; ++i) p *= 2.0;
+  return (p - 8.0) / cx_fact(k + 4);
+}
+
+template <class R>
+__device__ __forceinline__ void case1_coeffs(R nu0, R rho0, R a, R b, R T, R out[4]) {
+  constexpr int N = Tr<R>::kSeries;
+  const R x = (R)2 * b * T, y = (a + b) * T;
+  R g1, g2, g3, g4;
+  if (x < (R)2) {
+    const R mx = -x;
+    R s1 = (R)g1c(N), s2 = (R)g2c(N);
+#pragma unroll
+    for (int k = N - 1; k >= 0; --k) {
+      s1 = s1 * mx + (R)g1c(k);
+      s2 = s2 * mx + (R)g2c(k);
+    }
+    g1 = s1;
+    g2 = s2;
+  } else {
+    const R e = m_exp(-x), ix = (R)1 / x, ix3 = ix * ix * ix;
+    g1 = ((x * x * (R)0.5 - x + (R)1) - e) * ix3;
+    g2 = ((R)2 * (e - (R)1) + x * (e + (R)1)) * ix3;
+  }
+  if (y < (R)2) {
+    const R my = -y;
+    R s3 = (R)g3c(N), s4 = (R)g4c(N);
+#pragma unroll
+    for (int k = N - 1; k >= 0; --k) {
+      s3 = s3 * my + (R)g3c(k);
+      s4 = s4 * my + (R)g4c(k);
+    }
+    g3 = s3;
+    g4 = s4;
+  } else {
+    const R e = m_exp(-y), iy = (R)1 / y, iy2 = iy * iy;
+    g3 = (e - (R)1 + y) * iy2;
+    g4 = (m_exp(-(R)2 * y) - (R)8 * e + ((R)7 + (R)2 * y * (y - (R)3))) * iy2 * iy2;
+  }
+  out[0] = (R)6 * nu0 * nu0 * g1;
+  out[1] = (R)6 * nu0 * nu0 * g2;
+  out[2] = (R)2 * nu0 * rho0 * g3;
+  out[3] = (R)3 * nu0 * nu0 * rho0 * rho0 * g4;
+}
+
+// ---------------------------------------------------------------------------
+// Case II.  In scaled time tau = t/T every integrand is a polynomial in tau
+// times e^{-x tau}, x in {A+B, B, 2B, A} (A = aT, B = bT), so each function is
+// a combination of phi_m(x) = int_0^1 tau^m e^{-x tau} dtau.  For x < 5,
+// phi_m(x) = m! e^{-x} S_m(x) with S_m(x) = sum_n x^n/(m+n+1)! (positive
+// terms; S_{m-1} = 1/m! + x S_m downwards); for x >= 5 the upward recurrence
+// phi_m = (m phi_{m-1} - e^{-x})/x is stable.
+// ---------------------------------------------------------------------------
+template <class R, int M>
+__device__ __forceinline__ void phi_vec(R x, R* phi) {
+  const R e = m_exp(-x);
+  if (x < (R)5) {
+    constexpr int N = Tr<R>::kSeries;
+    R s = (R)1;
+#pragma unroll
+    for (int n = N; n >= 1; --n) s = (R)1 + s * x * (R)(1.0 / (M + 1 + n));
+    R S = s * (R)(1.0 / cx_fact(M + 1));
+    phi[M] = (R)cx_fact(M) * e * S;
+#pragma unroll
+    for (int m = M - 1; m >= 0; --m) {
+      S = (R)(1.0 / cx_fact(m + 1)) + x * S;
+      phi[m] = (R)cx_fact(m) * e * S;
+    }
+  } else {
+    const R ix = (R)1 / x;
+    phi[0] = ((R)1 - e) * ix;
+#pragma unroll
+    for (int m = 1; m <= M; ++m) phi[m] = ((R)m * phi[m - 1] - e) * ix;
+  }
+}
+
+// nu1^2 = 3 int_0^1 (1-tau)^2 nu^2,  nu2^2 = 6 int_0^1 (1-tau) tau nu^2,
+// eta1 = 2 int_0^1 (1-tau) nu rho, with nu = (nu0 + Qn tau) e^{-B tau} + dn,
+// rho = (rho0 + Qr tau) e^{-A tau} + dr: polynomial coefficients expanded by
+// hand below.
+template <class R>
+__device__ __forceinline__ void case2_single(R rho0, R nu0, R A, R B, R dr, R dn, R Qr,
+                                             R Qn, R out3[3]) {
+  R f2B[5], fB[5], fA[5], fAB[5];
+  phi_vec<R, 4>((R)2 * B, f2B);
+  phi_vec<R, 3>(B, fB);
+  phi_vec<R, 2>(A, fA);
+  phi_vec<R, 3>(A + B, fAB);
+  // P = (nu0 + Qn t)^2 = p0 + p1 t + p2 t^2 ; Rn = nu0 + Qn t
+  const R p0 = nu0 * nu0, p1 = (R)2 * nu0 * Qn, p2 = Qn * Qn;
+  // (1-t)^2 P
+  const R a0 = p0, a1 = p1 - (R)2 * p0, a2 = p2 - (R)2 * p1 + p0, a3 = p1 - (R)2 * p2, a4 = p2;
+  // (1-t)^2 Rn
+  const R b0 = nu0, b1 = Qn - (R)2 * nu0, b2 = nu0 - (R)2 * Qn, b3 = Qn;
+  const R nu1 = (R)3 * (a0 * f2B[0] + a1 * f2B[1] + a2 * f2B[2] + a3 * f2B[3] + a4 * f2B[4] +
+                        (R)2 * dn * (b0 * fB[0] + b1 * fB[1] + b2 * fB[2] + b3 * fB[3]) +
+                        dn * dn / (R)3);
+  // (1-t) t P = p0 t + (p1 - p0) t^2 + (p2 - p1) t^3 - p2 t^4
+  // (1-t) t Rn = nu0 t + (Qn - nu0) t^2 - Qn t^3
+  const R nu2 = (R)6 * (p0 * f2B[1] + (p1 - p0) * f2B[2] + (p2 - p1) * f2B[3] - p2 * f2B[4] +
+                        (R)2 * dn * (nu0 * fB[1] + (Qn - nu0) * fB[2] - Qn * fB[3]) +
+                        dn * dn / (R)6);
+  // nu rho = Kp(t) e^{-(A+B)t} + dr Rn e^{-Bt} + dn (rho0 + Qr t) e^{-At} + dn dr
+  // Kp = k0 + k1 t + k2 t^2
+  const R k0 = nu0 * rho0, k1 = nu0 * Qr + Qn * rho0, k2 = Qn * Qr;
+  // (1-t) Kp = k0 + (k1-k0) t + (k2-k1) t^2 - k2 t^3 ; (1-t) Rn ; (1-t)(rho0 + Qr t)
+  const R eta1 = (R)2 * (k0 * fAB[0] + (k1 - k0) * fAB[1] + (k2 - k1) * fAB[2] - k2 * fAB[3] +
+                         dr * (nu0 * fB[0] + (Qn - nu0) * fB[1] - Qn * fB[2]) +
+                         dn * (rho0 * fA[0] + (Qr - rho0) * fA[1] - Qr * fA[2]) +
+                         dn * dr / (R)2);
+  out3[0] = nu1;
+  out3[1] = nu2;
+  out3[2] = eta1;
+}
+
+// G(s) = int_0^s nu(Tu) rho(Tu) du at one node s, from
+// int_0^s u^m e^{-xu} du = s^{m+1} phi_m(x s).
+template <class R>
+__device__ __forceinline__ R case2_G(R s, R rho0, R nu0, R A, R B, R dr, R dn, R Qr, R Qn) {
+  R pAB[3], pB[2], pA[2];
+  phi_vec<R, 2>((A + B) * s, pAB);
+  phi_vec<R, 1>(B * s, pB);
+  phi_vec<R, 1>(A * s, pA);
+  const R k0 = nu0 * rho0, k1 = nu0 * Qr + Qn * rho0, k2 = Qn * Qr;
+  const R s2 = s * s;
+  return s * (k0 * pAB[0] + s * k1 * pAB[1] + s2 * k2 * pAB[2]) +
+         dr * s * (nu0 * pB[0] + s * Qn * pB[1]) + dn * s * (rho0 * pA[0] + s * Qr * pA[1]) +
+         dn * dr * s;
+}
+
+// Number of geometric panels [4^-(P-1) .. 1] the eta2^2 rule uses: enough
+// that the boundary layer of width 1/(A+B) at s = 0 spans whole panels.
+template <class R>
+__device__ __forceinline__ int case2_panels(R A, R B) {
+  const R x = A + B;
+  int p = 1;
+  R edge = (R)1;
+  while (p < 7 && edge * x > (R)1) {
+    edge *= (R)0.25;
+    ++p;
+  }
+  return p;
+}
+
+// eta2^2 = 12 int_0^1 (1 - s) G(s)^2 ds over panel `panel` (0 = [0, 4^-(P-1)],
+// P-1 = [1/4, 1]) by the Gauss-Legendre rule of the precision.
+template <class R>
+__device__ __forceinline__ R case2_eta2_panel(int panel, int npanels, R rho0, R nu0, R A, R B,
+                                              R dr, R dn, R Qr, R Qn) {
+  constexpr int NG = Tr<R>::kGauss;
+  R lo = (R)0, hi = (R)1;
+  for (int k = npanels - 1; k > panel; --k) hi *= (R)0.25;
+  if (panel > 0) lo = hi * (R)0.25;
+  const R c = (R)0.5 * (lo + hi), h = (R)0.5 * (hi - lo);
+  R acc = (R)0;
+#pragma unroll 2
+  for (int i = 0; i < NG; ++i) {
+    const R s = c + h * (R)kGaussRule<NG>.x[i];
+    const R G = case2_G<R>(s, rho0, nu0, A, B, dr, dn, Qr, Qn);
+    acc += (R)kGaussRule<NG>.w[i] * ((R)1 - s) * G * G;
+  }
+  return (R)12 * h * acc;
+}
+
+// All four Case II functions at T (single thread).
+template <class R, class P>
+__device__ __forceinline__ void case2_coeffs(const P* x, R T, R out[4]) {
+  const R rho0 = (R)x[2], nu0 = (R)x[3], A = (R)x[4] * T, B = (R)x[5] * T;
+  const R dr = (R)x[6], dn = (R)x[7], Qr = (R)x[8] * T, Qn = (R)x[9] * T;
+  case2_single<R>(rho0, nu0, A, B, dr, dn, Qr, Qn, out);
+  const int np = case2_panels<R>(A, B);
+  R e2 = (R)0;
+  for (int p = 0; p < np; ++p) e2 += case2_eta2_panel<R>(p, np, rho0, nu0, A, B, dr, dn, Qr, Qn);
+  out[3] = e2;
+}
+
+// Per-maturity polynomial for DYN_I / DYN_II (single thread).
+template <class R, bool CASE2, class P>
+__device__ __forceinline__ PolyCoef<R> dynamic_coef(const P* x, R l2f, R T) {
+  R c[4];
+  if constexpr (CASE2) {
+    case2_coeffs<R, P>(x, T, c);
+  } else {
+    case1_coeffs<R>((R)x[3], (R)x[2], (R)x[4], (R)x[5], T, c);
+  }
+  return dynamic_poly<R>((R)x[0], (R)x[1], l2f, T, c[0], c[1], c[2], c[3]);
+}
+
+// Case II feasibility: rho(t) in [-1, 1], nu(t) > 0 on [0, Tmax] (extremes
+// at the ends or at the stationary point t* = 1/k - c/q of
+// g(t) = (c + q t) e^{-k t} + d).
+template <class R>
+__device__ __forceinline__ void g_range(R c, R q, R k, R d, R Tmax, R& gmin, R& gmax) {
+  const R g0 = c + d;
+  const R g1 = (c + q * Tmax) * m_exp(-k * Tmax) + d;
+  gmin = g0 < g1 ? g0 : g1;
+  gmax = g0 < g1 ? g1 : g0;
+  if (k != (R)0 && q != (R)0) {
+    const R ts = (R)1 / k - c / q;
+    if (ts > (R)0 && ts < Tmax) {
+      const R gs = (c + q * ts) * m_exp(-k * ts) + d;
+      gmin = gs < gmin ? gs : gmin;
+      gmax = gs > gmax ? gs : gmax;
+    }
+  }
+}
+template <class R, class P>
+__device__ __forceinline__ bool case2_feasible(const P* x, R Tmax) {
+  R rmin, rmax, nmin, nmax;
+  g_range<R>((R)x[2], (R)x[8], (R)x[4], (R)x[6], Tmax, rmin, rmax);
+  g_range<R>((R)x[3], (R)x[9], (R)x[5], (R)x[7], Tmax, nmin, nmax);
+  return rmin >= (R)-1 && rmax <= (R)1 && nmin > (R)0;
+}
+
+}  // namespace sabr

@@ -1,0 +1,93 @@
+"""GPU parity of sabr_mc_price (Sec. 4) with the FP64 oracle on identical
+Philox streams: 1e-5 absolute in FP32 (forward 1), 1e-10 in FP64; and, at
+2^24 paths where the oracle would take minutes, the properties that hold at
+any size (Black limit, martingale, put-call identity)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2407_20713_gb300 as sg
+from helpers import black_call
+
+pytestmark = pytest.mark.gpu
+
+TOL = {sg.FP32: 1e-5, sg.FP64: 1e-10}
+
+
+def quotes():
+    T = np.repeat([0.25, 0.5, 1.0, 1.37], 4)
+    K = np.tile([0.8, 0.95, 1.05, 1.3], 4)
+    ic = np.tile([1, 1, 0, 1], 4).astype(np.int8)
+    return T, K, ic
+
+
+PARAMS = {
+    sg.HAGAN: [0.3, 0.6, -0.4, 0.7],
+    sg.DYN_I: [0.3, 0.7, -0.6, 0.9, 0.5, 1.2],
+    sg.DYN_II: [0.3, 0.8, -0.5, 0.7, 1.1, 0.6, 0.1, 0.2, 0.25, -0.2],
+}
+
+
+@pytest.mark.parametrize("prec", [sg.FP32, sg.FP64])
+@pytest.mark.parametrize("model", [sg.HAGAN, sg.DYN_I, sg.DYN_II])
+def test_mc_matches_oracle_on_the_same_streams(model, prec):
+    T, K, ic = quotes()
+    disc = np.linspace(0.99, 0.9, T.size)
+    n_paths = 3 * 4096 + 77  # ragged against blocks and warps
+    p = PARAMS[model]
+    ref, rse = O.mc_price(model, p, 1.0, T, K, is_call=ic, disc=disc, n_paths=n_paths, steps_per_year=250,
+                          seed=12345, n_threads=8)
+    got, gse = sg.mc_price(model, p, 1.0, T, K, is_call=ic, discount=disc, n_paths=n_paths, steps_per_year=250,
+                           seed=12345, prec=prec)
+    got, gse = got.cpu().numpy(), gse.cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= TOL[prec], np.abs(got - ref)
+    assert np.max(np.abs(gse - rse)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [sg.FP32, sg.FP64])
+def test_mc_absorption_heavy_case_matches_oracle(prec):
+    # beta = 0 with a large alpha: many paths hit zero and are absorbed
+    T = np.array([0.5, 1.0, 2.0, 2.0])
+    K = np.array([0.5, 1.0, 1.0, 0.2])
+    ic = np.array([1, 1, 0, 0], dtype=np.int8)
+    p = [0.9, 0.0, -0.2, 0.5]
+    ref, _ = O.mc_price(O.HAGAN, p, 1.0, T, K, is_call=ic, n_paths=5000, steps_per_year=100, seed=8, n_threads=8)
+    got, _ = sg.mc_price(sg.HAGAN, p, 1.0, T, K, is_call=ic, n_paths=5000, steps_per_year=100, seed=8, prec=prec)
+    assert np.max(np.abs(got.cpu().numpy() - ref)) <= TOL[prec]
+
+
+def test_mc_full_size_black_limit_and_identities():
+    n = 1 << 24
+    T = np.array([0.5, 0.5, 1.0, 1.0, 1.0])
+    K = np.array([1.0, 1.2, 1e-12, 0.9, 0.9])
+    ic = np.array([1, 1, 1, 1, 0], dtype=np.int8)
+    # nu = 0, beta = 1: geometric Brownian motion, exact under log-Euler
+    p = [0.25, 1.0, -0.3, 0.0]
+    got, se = sg.mc_price(sg.HAGAN, p, 1.0, T, K, is_call=ic, n_paths=n, steps_per_year=250, seed=1)
+    got, se = got.cpu().numpy(), se.cpu().numpy()
+    ref = black_call(1.0, K[:2], T[:2], 0.25)
+    assert np.all(np.abs(got[:2] - ref) <= 4 * se[:2])
+    assert abs(got[2] - 1.0) <= 4 * se[2]                      # martingale
+    assert abs((got[3] - got[4]) - (got[2] - 0.9)) <= 1e-6     # put-call, pathwise
+    # full SABR dynamics: martingale and put-call identity still hold
+    got, se = sg.mc_price(sg.HAGAN, [0.3, 0.5, -0.5, 0.8], 1.0, T, K, is_call=ic, n_paths=n,
+                          steps_per_year=250, seed=2)
+    got, se = got.cpu().numpy(), se.cpu().numpy()
+    assert abs(got[2] - 1.0) <= 4 * se[2]
+    assert abs((got[3] - got[4]) - (got[2] - 0.9)) <= 1e-6
+
+
+def test_mc_is_deterministic_and_validates():
+    T, K, ic = quotes()
+    a, _ = sg.mc_price(sg.HAGAN, PARAMS[sg.HAGAN], 1.0, T, K, is_call=ic, n_paths=10000, seed=5)
+    b, _ = sg.mc_price(sg.HAGAN, PARAMS[sg.HAGAN], 1.0, T, K, is_call=ic, n_paths=10000, seed=5)
+    assert np.array_equal(a.cpu().numpy(), b.cpu().numpy())
+    got, _ = sg.mc_price(sg.HAGAN, PARAMS[sg.HAGAN], 1.0, [1.0], [1.0], n_paths=2, seed=5)
+    ref, _ = O.mc_price(O.HAGAN, PARAMS[sg.HAGAN], 1.0, [1.0], [1.0], n_paths=2, seed=5)
+    assert abs(got.item() - ref[0]) <= 1e-5
+    with pytest.raises(sg.SabrError):   # rho(t) leaves [-1, 1]
+        sg.mc_price(sg.DYN_II, [0.3, 0.8, 0.9, 0.7, 0.0, 0.6, 0.3, 0.2, 0.0, 0.0], 1.0, [1.0], [1.0])
+    with pytest.raises(sg.SabrError):
+        sg.mc_price(sg.HAGAN, PARAMS[sg.HAGAN], 1.0, np.ones(513), np.ones(513))
+    with pytest.raises(sg.SabrError):
+        sg.mc_price(sg.HAGAN, PARAMS[sg.HAGAN], 1.0, [1.0], [1.0], n_paths=1)

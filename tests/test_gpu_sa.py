@@ -1,0 +1,170 @@
+"""GPU parity of sabr_calibrate / sabr_calibrate_batch (Sec. 5 synchronous
+parallel SA) with the FP64 oracle.
+
+FP64: the same Philox streams and operation order give the oracle's
+trajectory, so best point, restart point and counters agree to rounding.
+FP32: trajectories part ways, so the bar is the final misfit within 1% of the
+oracle's on a problem the method solves to its minimum, and recovery of the
+synthetic truth."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2407_20713_gb300 as sg
+
+pytestmark = pytest.mark.gpu
+
+K15 = 0.6 + 0.8 * np.arange(15) / 14
+T15 = np.ones(15)
+TRUTH = [0.2, 0.7, -0.4, 0.5]
+LO4 = [1e-6, 0.0, -1 + 1e-6, 1e-6]
+HI4 = [2.0, 1.0, 1 - 1e-6, 3.0]
+
+
+def market(model=O.HAGAN, truth=TRUTH, T=T15, K=K15, noise=1e-4, seed=20240720):
+    rng = np.random.default_rng(seed)
+    return O.implied_vol(model, truth, 1.0, T, K) + rng.normal(0, noise, len(T))
+
+
+def run_both(model, T, K, mkt, lo, hi, prec=sg.FP64, **kw):
+    pb = sg.CalibrationProblem(model=model, T=T, K=K, market=mkt, lo=lo, hi=hi, prec=prec, **kw)
+    g = sg.calibrate(pb)
+    o = O.sa_calibrate(model, 1.0, T, K, mkt, lo, hi, n_chains=pb.n_chains, T0=pb.T0, factor=pb.factor,
+                       n_levels=pb.n_levels, chain_len=pb.chain_len, step0=pb.step0, step_min=pb.step_min,
+                       seed=pb.seed, x0=pb.x0, n_threads=8)
+    return g, o
+
+
+def dyn_surface(model, n_mats=3, n_strikes=5):
+    mats = np.array([0.25, 1.0, 3.0, 0.5, 2.0, 5.0][:n_mats])
+    T = np.repeat(mats, n_strikes)
+    K = np.tile(np.linspace(0.8, 1.25, n_strikes), n_mats)
+    if model == O.DYN_I:
+        truth = [0.25, 0.8, -0.5, 0.7, 0.6, 0.9]
+        lo = [0.05, 0.5, -1.0, 0.01, 0.0, 0.0]
+        hi = [0.6, 1.0, 1.0, 1.5, 3.0, 3.0]
+    else:
+        truth = [0.25, 0.8, -0.4, 0.6, 0.8, 0.9, 0.1, 0.15, 0.2, -0.1]
+        lo = [0.05, 0.5, -1.0, 0.01, 0.0, 0.0, -0.5, -0.3, -1.0, -1.0]
+        hi = [0.6, 1.0, 1.0, 1.5, 3.0, 3.0, 0.5, 0.5, 1.0, 1.0]
+    return T, K, market(model, truth, T, K, seed=11), lo, hi
+
+
+@pytest.mark.parametrize("model", [sg.HAGAN, sg.OBLOJ, sg.EXPANDED])
+def test_fp64_static_trajectory_is_the_oracle_trajectory(model):
+    mkt = market()
+    g, o = run_both(model, T15, K15, mkt, LO4, HI4, n_chains=64, n_levels=20, chain_len=30, seed=5)
+    assert g.status == 0
+    assert g.n_evals == o["n_evals"] and g.n_accepts == o["n_accepts"]
+    np.testing.assert_allclose(g.params, o["params"], rtol=1e-10, atol=1e-14)
+    np.testing.assert_allclose(g.restart_params, o["restart_params"], rtol=1e-10, atol=1e-14)
+    assert g.misfit == pytest.approx(o["misfit"], rel=1e-10)
+    assert g.misfit_fp64 == pytest.approx(o["misfit"], rel=1e-10)
+
+
+@pytest.mark.parametrize("model", [sg.DYN_I, sg.DYN_II])
+def test_fp64_dynamic_trajectory_is_the_oracle_trajectory(model):
+    T, K, mkt, lo, hi = dyn_surface(model)
+    g, o = run_both(model, T, K, mkt, lo, hi, n_chains=16, n_levels=6, chain_len=12, seed=9)
+    assert g.status == 0
+    assert g.n_evals == o["n_evals"] and g.n_accepts == o["n_accepts"]
+    np.testing.assert_allclose(g.params, o["params"], rtol=1e-9, atol=1e-13)
+    assert g.misfit == pytest.approx(o["misfit"], rel=1e-9)
+
+
+def test_fp32_two_parameter_fit_within_one_percent_of_oracle():
+    mkt = market()
+    lo = [0.2, 0.7, -1 + 1e-6, 1e-6]
+    hi = [0.2, 0.7, 1 - 1e-6, 3.0]
+    g, o = run_both(sg.HAGAN, T15, K15, mkt, lo, hi, prec=sg.FP32, n_chains=64, seed=3)
+    assert abs(g.misfit_fp64 - o["misfit"]) <= 0.01 * o["misfit"]
+    np.testing.assert_allclose(g.params[2:], o["params"][2:], atol=2e-3)
+
+
+def test_fp32_recovers_the_synthetic_smile():
+    # beta fixed (the paper's usual practice, Sec. 3); noise 1e-4 in vol
+    mkt = market()
+    lo = [1e-6, 0.7, -1 + 1e-6, 1e-6]
+    hi = [2.0, 0.7, 1 - 1e-6, 3.0]
+    pb = sg.CalibrationProblem(model=sg.HAGAN, T=T15, K=K15, market=mkt, lo=lo, hi=hi, prec=sg.FP32,
+                               n_chains=256, seed=1)
+    g = sg.calibrate(pb)
+    fit = O.implied_vol(O.HAGAN, g.params, 1.0, T15, K15)
+    true = O.implied_vol(O.HAGAN, TRUTH, 1.0, T15, K15)
+    assert np.max(np.abs(fit - true)) <= 3e-4
+    assert abs(g.params[2] - TRUTH[2]) <= 0.05 and abs(g.params[3] - TRUTH[3]) / TRUTH[3] <= 0.05
+
+
+def test_fp32_full_smile_reports_error_against_oracle():
+    mkt = market()
+    g, o = run_both(sg.HAGAN, T15, K15, mkt, LO4, HI4, prec=sg.FP32, n_chains=64, seed=7)
+    # the FP32 in-loop misfit and its FP64 re-score agree to FP32 rounding
+    assert abs(g.misfit - g.misfit_fp64) <= 1e-3 * g.misfit_fp64 + 1e-9
+    # both land in the same basin: the model fit is within a few noise levels
+    for params in (g.params, o["params"]):
+        fit = O.implied_vol(O.HAGAN, params, 1.0, T15, K15)
+        assert np.sqrt(np.mean((fit - mkt) ** 2)) <= 2e-3
+
+
+@pytest.mark.parametrize("prec", [sg.FP32, sg.FP64])
+def test_result_is_the_same_alone_and_in_a_batch(prec):
+    mkt = market()
+    T, K, mk2, lo2, hi2 = dyn_surface(O.DYN_I)
+    a = sg.CalibrationProblem(model=sg.HAGAN, T=T15, K=K15, market=mkt, lo=LO4, hi=HI4, prec=prec,
+                              n_chains=300, n_levels=8, chain_len=20, seed=21)
+    b = sg.CalibrationProblem(model=sg.DYN_I, T=T, K=K, market=mk2, lo=lo2, hi=hi2, prec=prec,
+                              n_chains=40, n_levels=5, chain_len=10, seed=4)
+    c = sg.CalibrationProblem(model=sg.HAGAN, T=T15[:7], K=K15[:7], market=mkt[:7], lo=LO4, hi=HI4,
+                              prec=prec, n_chains=1000, n_levels=3, chain_len=5, seed=99)
+    alone = sg.calibrate(a)
+    batch = sg.calibrate_batch([c, a, b])
+    assert np.array_equal(alone.params, batch[1].params)
+    assert alone.misfit == batch[1].misfit and alone.n_evals == batch[1].n_evals
+    assert alone.n_accepts == batch[1].n_accepts
+
+
+def test_graph_replay_equals_direct_launches_and_repeats():
+    mkt = market()
+    pbs = [sg.CalibrationProblem(model=sg.HAGAN, T=T15, K=K15, market=mkt, lo=LO4, hi=HI4,
+                                 n_chains=128, n_levels=10, chain_len=20, seed=s) for s in range(3)]
+    direct = sg.calibrate_batch(pbs)
+    plan = sg.Plan(pbs, use_graph=True)
+    plan.run()
+    r1 = plan.results()
+    plan.run()
+    r2 = plan.results()
+    n_launch, ms = plan.stats()
+    plan.close()
+    for x, y, z in zip(direct, r1, r2):
+        assert np.array_equal(x.params, y.params) and np.array_equal(y.params, z.params)
+        assert x.misfit == y.misfit == z.misfit and x.n_evals == y.n_evals == z.n_evals
+    assert n_launch == 1 + 10 + 1 and ms > 0
+
+
+def test_edge_cases():
+    mkt = market()
+    # no levels: the start point comes back
+    g = sg.calibrate(sg.CalibrationProblem(model=sg.HAGAN, T=T15, K=K15, market=mkt, lo=LO4, hi=HI4,
+                                           n_levels=0, x0=TRUTH))
+    np.testing.assert_allclose(g.params, TRUTH, rtol=1e-7)
+    assert g.n_evals == 0
+    # one chain, one quote, a chain count that leaves a ragged last block
+    for nc in (1, 257):
+        g, o = run_both(sg.HAGAN, T15[:1], K15[:1], mkt[:1], LO4, HI4, n_chains=nc, n_levels=3, chain_len=4,
+                        seed=2)
+        assert g.n_evals == o["n_evals"]
+        np.testing.assert_allclose(g.params, o["params"], rtol=1e-10)
+    # fixed coordinates never move
+    lo = [0.2, 0.7, -0.9, 0.1]
+    hi = [0.2, 0.7, 0.5, 1.5]
+    g = sg.calibrate(sg.CalibrationProblem(model=sg.HAGAN, T=T15, K=K15, market=mkt, lo=lo, hi=hi,
+                                           n_levels=5, chain_len=10, prec=sg.FP32))
+    assert g.params[0] == np.float32(0.2) and g.params[1] == np.float32(0.7)
+    # invalid input is refused before any launch
+    with pytest.raises(sg.SabrError):
+        sg.calibrate(sg.CalibrationProblem(model=sg.HAGAN, T=T15, K=K15, market=-mkt, lo=LO4, hi=HI4))
+    with pytest.raises(sg.SabrError):
+        sg.calibrate(sg.CalibrationProblem(model=sg.HAGAN, T=T15, K=K15, market=mkt, lo=HI4, hi=LO4))
+    with pytest.raises(sg.SabrError):
+        sg.calibrate(sg.CalibrationProblem(model=sg.HAGAN, T=T15, K=K15, market=mkt, lo=LO4, hi=HI4,
+                                           n_chains=0))
