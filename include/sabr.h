@@ -203,6 +203,58 @@ sabr_status sabr_plan_stats(sabr_plan* plan, int64_t* launches_per_run,
                             double* level_kernel_ms);
 void sabr_plan_destroy(sabr_plan* plan);
 
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of calibration requests (Sec. 5 engines).
+ * A server owns a worker thread, a device-memory pool and a stream.  Each
+ * worker step admits queued requests while the pool and max_active allow
+ * (admission by device memory), then advances every resident formula-cost
+ * request by one temperature level in one set of persistent launches
+ * (replayed from a captured CUDA graph when use_graph != 0) and every
+ * resident MC-cost request by one proposal wave on a second stream, so that
+ * requests that arrive while others run join them on the device.  Finished
+ * requests release their memory at once.  A request's result does not depend
+ * on what else is resident (same result as sabr_calibrate).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int64_t device_bytes; /* pool for resident requests (>= 1 MiB)          */
+  int32_t max_queue;    /* waiting requests; submit returns EBUSY beyond   */
+  int32_t max_active;   /* resident requests, 1 .. 4096                    */
+  int32_t max_quotes;   /* largest formula request accepted, <= 4096       */
+  int32_t use_graph;    /* replay each step from a captured CUDA graph     */
+} sabr_server_config;
+
+typedef struct {
+  int64_t submitted, admitted, completed, cancelled, steps, kernel_launches;
+  int32_t queued, active;
+  int64_t pool_bytes_in_use;
+} sabr_server_stats;
+
+typedef struct sabr_server sabr_server;
+
+/* Creates the server on the current device (pool allocated here). */
+sabr_status sabr_server_create(const sabr_server_config* config, sabr_server** out);
+/* Deep-copies the host arrays of *problem; the caller may free them after
+ * return.  EBUSY if the queue is full, EINVAL for a malformed problem or one
+ * larger than the pool or max_quotes.  *ticket identifies the request. */
+sabr_status sabr_server_submit(sabr_server* server, const sabr_problem* problem,
+                               const sabr_bounds* bounds,
+                               const sabr_cooling* cooling, uint64_t seed,
+                               uint64_t* ticket);
+/* EAGAIN while queued or running; SABR_OK with *out filled when done;
+ * ECANCELLED, ENOTFOUND.  A finished ticket is released by the first poll or
+ * wait that returns it. */
+sabr_status sabr_server_poll(sabr_server* server, uint64_t ticket, sabr_result* out);
+/* Blocks up to timeout_ms (< 0: no limit) for the request; ETIMEOUT when the
+ * time runs out first. */
+sabr_status sabr_server_wait(sabr_server* server, uint64_t ticket, int64_t timeout_ms,
+                             sabr_result* out);
+/* Cancels a queued request (ECANCELLED for later polls); a resident one is
+ * cancelled at the next step boundary.  ENOTFOUND for unknown tickets. */
+sabr_status sabr_server_cancel(sabr_server* server, uint64_t ticket);
+sabr_status sabr_server_get_stats(sabr_server* server, sabr_server_stats* out);
+/* Stops the worker after the current step, drops what is left, frees all. */
+void sabr_server_destroy(sabr_server* server);
+
 /* Measurement utility (not part of the paper's method): throughput of the
  * arithmetic pipes on the current device, in operations per SM clock, from
  * loops of independent operations timed with the SM cycle counter:

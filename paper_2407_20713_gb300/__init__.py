@@ -9,5 +9,5 @@ Annealing calibration (Sec. 5), behind the C-ABI of include/sabr.h.
 from . import capi  # noqa: F401
 from .capi import (COST_MC_PRICE, COST_VOL, DYN_I, DYN_II, EXPANDED, FP32, FP64, HAGAN,  # noqa: F401
                    OBLOJ, SabrError)
-from .api import (CalibrationProblem, CalibrationResult, Plan, calibrate, calibrate_batch,  # noqa: F401
+from .api import (CalibrationProblem, CalibrationResult, Plan, Server, calibrate, calibrate_batch,  # noqa: F401
                   implied_vol, mc_price)

@@ -156,8 +156,11 @@ def _marshal(problems: List[CalibrationProblem]):
     B = (capi.Bounds * n)()
     C = (capi.Cooling * n)()
     S = (ctypes.c_uint64 * n)()
+    keep = []
     for i, pb in enumerate(problems):
         P[i], B[i], C[i], S[i] = pb.to_c()
+        keep.append(pb._keep)  # arrays stay alive while the C structs point at them
+    P._keep = keep
     return P, B, C, S
 
 
@@ -213,6 +216,59 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.sabr_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching calibration server (sabr_server_* of include/sabr.h)."""
+
+    def __init__(self, device_bytes=1 << 30, max_queue=1 << 20, max_active=256, max_quotes=512, use_graph=True):
+        self._lib = capi.load()
+        cfg = capi.ServerConfig(int(device_bytes), int(max_queue), int(max_active), int(max_quotes),
+                                1 if use_graph else 0)
+        h = ctypes.c_void_p()
+        capi.check(self._lib.sabr_server_create(ctypes.byref(cfg), ctypes.byref(h)), "sabr_server_create")
+        self._h = h
+        self._models = {}
+
+    def submit(self, problem: CalibrationProblem) -> int:
+        pr, b, c, seed = problem.to_c()
+        t = ctypes.c_uint64()
+        capi.check(self._lib.sabr_server_submit(self._h, ctypes.byref(pr), ctypes.byref(b), ctypes.byref(c), seed,
+                                                ctypes.byref(t)), "sabr_server_submit")
+        self._models[t.value] = problem.model
+        return t.value
+
+    def poll(self, ticket):
+        r = capi.Result()
+        st = self._lib.sabr_server_poll(self._h, ticket, ctypes.byref(r))
+        if st == capi.EAGAIN:
+            return None
+        capi.check(st, "sabr_server_poll")
+        return CalibrationResult.from_c(r, self._models.pop(ticket))
+
+    def wait(self, ticket, timeout_ms=-1):
+        r = capi.Result()
+        capi.check(self._lib.sabr_server_wait(self._h, ticket, int(timeout_ms), ctypes.byref(r)), "sabr_server_wait")
+        return CalibrationResult.from_c(r, self._models.pop(ticket))
+
+    def cancel(self, ticket):
+        capi.check(self._lib.sabr_server_cancel(self._h, ticket), "sabr_server_cancel")
+
+    def stats(self):
+        st = capi.ServerStats()
+        capi.check(self._lib.sabr_server_get_stats(self._h, ctypes.byref(st)), "sabr_server_get_stats")
+        return {name: getattr(st, name) for name, _ in capi.ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sabr_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -55,7 +55,13 @@ class Result(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("device_bytes", c_int64), ("max_queue", c_int32), ("max_active", c_int32),
-                ("max_chains_in_flight", c_int64), ("use_graph", c_int32)]
+                ("max_quotes", c_int32), ("use_graph", c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", c_int64), ("admitted", c_int64), ("completed", c_int64), ("cancelled", c_int64),
+                ("steps", c_int64), ("kernel_launches", c_int64), ("queued", c_int32), ("active", c_int32),
+                ("pool_bytes_in_use", c_int64)]
 
 
 # name -> (restype, argtypes)
@@ -76,6 +82,14 @@ SIGNATURES = {
     "sabr_plan_stats": (c_int, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_double)]),
     "sabr_plan_destroy": (None, [c_void_p]),
     "sabr_probe_pipe_rates": (c_int, [PD, c_int32, c_void_p]),
+    "sabr_server_create": (c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(c_void_p)]),
+    "sabr_server_submit": (c_int, [c_void_p, ctypes.POINTER(Problem), ctypes.POINTER(Bounds),
+                                   ctypes.POINTER(Cooling), c_uint64, ctypes.POINTER(c_uint64)]),
+    "sabr_server_poll": (c_int, [c_void_p, c_uint64, ctypes.POINTER(Result)]),
+    "sabr_server_wait": (c_int, [c_void_p, c_uint64, c_int64, ctypes.POINTER(Result)]),
+    "sabr_server_cancel": (c_int, [c_void_p, c_uint64]),
+    "sabr_server_get_stats": (c_int, [c_void_p, ctypes.POINTER(ServerStats)]),
+    "sabr_server_destroy": (None, [c_void_p]),
     "sabr_last_error": (ctypes.c_char_p, []),
 }
 

@@ -18,6 +18,8 @@
 
 #include "common.h"
 #include "engine.cuh"
+#include "engine_host.h"
+#include "mcsa_host.h"
 
 namespace sabr {
 
@@ -112,22 +114,20 @@ __global__ void sa_init_kernel(const ProblemDev* __restrict__ probs, const int* 
 // ---------------------------------------------------------------------------
 // One temperature level for every chain of a launch group.
 // ---------------------------------------------------------------------------
+// Block `blk` of problem P (staged in shared memory) runs level `level`.
+// Every thread of the block calls this.
 template <class R, int MODEL>
-__global__ void __launch_bounds__(kSaBlock) sa_level_kernel(const ProblemDev* __restrict__ probs,
-                                                           const int2* __restrict__ bmap, int level) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ ProblemDev P;
-  const int2 bm = bmap[blockIdx.x];
-  load_problem(probs, bm.x, &P);
-  if (level >= P.n_levels) return;
-
+__device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int level, unsigned char* smem) {
+  const int2 bm = make_int2(0, blk);
   unsigned char* rest;
   const SmemQuotes<R> sq = stage_quotes<R>(P, smem, blockDim.x, threadIdx.x, &rest);
   constexpr int D = Dim<MODEL>::value;
   const int G = P.G, cpb = P.cpb;
   const int g = threadIdx.x / G, lane = threadIdx.x % G;
-  R* coef = (R*)rest + (size_t)g * 3 * P.n_mats;
-  double* red_f = (double*)((R*)rest + (size_t)cpb * 3 * P.n_mats + 16);
+  // per-maturity polynomial slices exist only for the dynamic models
+  const int coef_m = (MODEL == SABR_DYN_I || MODEL == SABR_DYN_II) ? P.n_mats : 0;
+  R* coef = (R*)rest + (size_t)g * 3 * coef_m;
+  double* red_f = (double*)((R*)rest + (size_t)cpb * 3 * coef_m + 16);
   red_f = (double*)(((uintptr_t)red_f + 15) & ~(uintptr_t)15);
   R* red_x = (R*)(red_f + cpb);
   __syncthreads();
@@ -260,6 +260,35 @@ __global__ void __launch_bounds__(kSaBlock) sa_level_kernel(const ProblemDev* __
   }
 }
 
+template <class R, int MODEL>
+__global__ void __launch_bounds__(kSaBlock) sa_level_kernel(const ProblemDev* __restrict__ probs,
+                                                           const int2* __restrict__ bmap, int level) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ ProblemDev P;
+  const int2 bm = bmap[blockIdx.x];
+  load_problem(probs, bm.x, &P);
+  if (level >= P.n_levels) return;
+  sa_level_block<R, MODEL>(P, bm.y, level, smem);
+}
+
+// Grid-stride form for the server: work[w] = (problem, block, level) for
+// w < *n_work, read from device memory so one captured launch serves every
+// step whatever its mix of requests.
+template <class R, int MODEL>
+__global__ void __launch_bounds__(kSaBlock) sa_level_persistent(const ProblemDev* __restrict__ probs,
+                                                               const int4* __restrict__ work,
+                                                               const int* __restrict__ n_work) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ ProblemDev P;
+  const int nw = *n_work;
+  for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+    const int4 it = work[w];
+    load_problem(probs, it.x, &P);
+    if (it.z < P.n_levels) sa_level_block<R, MODEL>(P, it.y, it.z, smem);
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Best point over all chains, FP64 re-score, counters -> result.
 // One 256-thread block per problem.
@@ -367,25 +396,13 @@ __global__ void __launch_bounds__(kSaBlock) sa_finalize_kernel(const ProblemDev*
     P.result->misfit_fp64 = s;
   }
 }
-
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-namespace {
-
-size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
-
-struct Arena {
-  size_t size = 0;
-  size_t take(size_t bytes) {
-    size_t off = align_up(size, 256);
-    size = off + bytes;
-    return off;
-  }
-};
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Host copy of the Case II range test (feasibility of x0).
-void h_range(double c, double q, double k, double d, double Tmax, double& mn, double& mx) {
+static void h_range(double c, double q, double k, double d, double Tmax, double& mn, double& mx) {
   double g0 = c + d, g1 = (c + q * Tmax) * std::exp(-k * Tmax) + d;
   mn = std::min(g0, g1);
   mx = std::max(g0, g1);
@@ -398,7 +415,7 @@ void h_range(double c, double q, double k, double d, double Tmax, double& mn, do
     }
   }
 }
-bool h_feasible(int model, const double* x, double Tmax) {
+static bool h_feasible(int model, const double* x, double Tmax) {
   if (model != SABR_DYN_II) return true;
   double rmn, rmx, nmn, nmx;
   h_range(x[2], x[8], x[4], x[6], Tmax, rmn, rmx);
@@ -406,14 +423,15 @@ bool h_feasible(int model, const double* x, double Tmax) {
   return rmn >= -1.0 && rmx <= 1.0 && nmn > 0.0;
 }
 
-int next_pow2(int v) {
+static int next_pow2(int v) {
   int p = 1;
   while (p < v) p <<= 1;
   return p;
 }
 
-// Lanes per chain: about eight quotes per lane, widened while the whole batch
-// would not fill the GPU (fewer than 64k threads) and quotes remain to split.
+// About eight quotes per lane, widened while the whole batch would not fill
+// the GPU (fewer than 64k threads) and quotes remain to split; the dynamic
+// models take at least one lane per maturity.
 int choose_lanes(int n_quotes, int n_mats, int model, long long batch_chains) {
   if (const char* e = std::getenv("SABR_LANES")) {
     int g = std::atoi(e);
@@ -427,152 +445,32 @@ int choose_lanes(int n_quotes, int n_mats, int model, long long batch_chains) {
   return G;
 }
 
-size_t level_smem_bytes(int prec, int Q, int M, int cpb) {
+size_t level_smem_bytes(int prec, int model, int Q, int M, int cpb) {
   const size_t rs = prec == SABR_FP64 ? 8 : 4;
+  const size_t cm = (model == SABR_DYN_I || model == SABR_DYN_II) ? (size_t)M : 0;
   size_t b = (5 * (size_t)Q + M) * rs + 4 * (size_t)Q;
   b = align_up(b, 16);
-  b += (size_t)cpb * 3 * M * rs + 16 * rs;
+  b += (size_t)cpb * 3 * cm * rs + 16 * rs;
   b = align_up(b, 16) + 16;
   b += (size_t)cpb * 8 + (size_t)cpb * kMaxD * rs;
   return align_up(b, 16) + 64;
 }
 
-}  // namespace
+size_t init_smem_bytes(const HostProblem& h) { return level_smem_bytes(h.prec, SABR_DYN_I, h.n_quotes, h.n_mats, 1); }
 
-struct LaunchGroup {
-  int prec = 0, model = 0;
-  std::vector<int> problems;
-  int total_blocks = 0;
-  int max_levels = 0;
-  size_t smem_level = 0, smem_init = 0;
-  int2* d_bmap = nullptr;
-  int* d_plist = nullptr;
-};
-
-}  // namespace sabr
-
-struct sabr_plan {
-  int device = 0;
-  int n = 0;
-  void* arena = nullptr;
-  sabr::ProblemDev* d_probs = nullptr;
-  sabr_result* d_results = nullptr;
-  sabr_result* h_results = nullptr;
-  std::vector<sabr::LaunchGroup> groups;
-  int max_levels = 0;
-  bool use_graph = false;
-  cudaGraphExec_t exec = nullptr;
-  cudaStream_t own_stream = nullptr;
-  cudaEvent_t ev_lv0 = nullptr, ev_lv1 = nullptr, ev_done = nullptr;
-  int64_t launches = 0;
-  int64_t level_launches = 0;
-  bool ran = false;
-};
-
-namespace sabr {
-
-template <class R, int MODEL>
-static void set_smem_attr(size_t bytes) {
-  cudaFuncSetAttribute(sa_level_kernel<R, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)bytes);
-  cudaFuncSetAttribute(sa_init_kernel<R, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)bytes);
-}
-
-template <class R>
-static void set_smem_attr_model(int model, size_t bytes) {
-  switch (model) {
-    case SABR_HAGAN: set_smem_attr<R, SABR_HAGAN>(bytes); break;
-    case SABR_OBLOJ: set_smem_attr<R, SABR_OBLOJ>(bytes); break;
-    case SABR_EXPANDED: set_smem_attr<R, SABR_EXPANDED>(bytes); break;
-    case SABR_DYN_I: set_smem_attr<R, SABR_DYN_I>(bytes); break;
-    default: set_smem_attr<R, SABR_DYN_II>(bytes); break;
-  }
-}
-
-template <class R, int MODEL>
-static int64_t enqueue_group(const sabr_plan* p, const LaunchGroup& g, cudaStream_t s, int phase,
-                             int level) {
-  if (phase == 0) {
-    sa_init_kernel<R, MODEL><<<(int)g.problems.size(), 32, g.smem_init, s>>>(p->d_probs, g.d_plist);
-    return 1;
-  }
-  if (phase == 1) {
-    if (level >= g.max_levels) return 0;
-    sa_level_kernel<R, MODEL><<<g.total_blocks, kSaBlock, g.smem_level, s>>>(p->d_probs, g.d_bmap, level);
-    return 1;
-  }
-  sa_finalize_kernel<R, MODEL><<<(int)g.problems.size(), kSaBlock, 0, s>>>(p->d_probs, g.d_plist);
-  return 1;
-}
-
-template <class R>
-static int64_t enqueue_model(const sabr_plan* p, const LaunchGroup& g, cudaStream_t s, int phase, int level) {
-  switch (g.model) {
-    case SABR_HAGAN: return enqueue_group<R, SABR_HAGAN>(p, g, s, phase, level);
-    case SABR_OBLOJ: return enqueue_group<R, SABR_OBLOJ>(p, g, s, phase, level);
-    case SABR_EXPANDED: return enqueue_group<R, SABR_EXPANDED>(p, g, s, phase, level);
-    case SABR_DYN_I: return enqueue_group<R, SABR_DYN_I>(p, g, s, phase, level);
-    default: return enqueue_group<R, SABR_DYN_II>(p, g, s, phase, level);
-  }
-}
-
-// The whole calibration of a plan, enqueued on s.
-static sabr_status enqueue_plan(sabr_plan* p, cudaStream_t s, bool capturing) {
-  int64_t launches = 0, level_launches = 0;
-  for (auto& g : p->groups)
-    launches += g.prec == SABR_FP64 ? enqueue_model<double>(p, g, s, 0, 0) : enqueue_model<float>(p, g, s, 0, 0);
-  if (capturing)
-    SABR_CUDA(cudaEventRecordWithFlags(p->ev_lv0, s, cudaEventRecordExternal));
-  else
-    SABR_CUDA(cudaEventRecord(p->ev_lv0, s));
-  for (int lv = 0; lv < p->max_levels; ++lv)
-    for (auto& g : p->groups) {
-      int64_t k = g.prec == SABR_FP64 ? enqueue_model<double>(p, g, s, 1, lv) : enqueue_model<float>(p, g, s, 1, lv);
-      launches += k;
-      level_launches += k;
-    }
-  if (capturing)
-    SABR_CUDA(cudaEventRecordWithFlags(p->ev_lv1, s, cudaEventRecordExternal));
-  else
-    SABR_CUDA(cudaEventRecord(p->ev_lv1, s));
-  for (auto& g : p->groups)
-    launches += g.prec == SABR_FP64 ? enqueue_model<double>(p, g, s, 2, 0) : enqueue_model<float>(p, g, s, 2, 0);
-  SABR_CUDA(cudaGetLastError());
-  SABR_CUDA(cudaMemcpyAsync(p->h_results, p->d_results, sizeof(sabr_result) * p->n,
-                            cudaMemcpyDeviceToHost, s));
-  p->launches = launches;
-  p->level_launches = level_launches;
-  return SABR_OK;
-}
-
-// Validation and FP64 preprocessing of one problem.
-struct HostProblem {
-  int model, prec, cost, d, n_quotes, n_mats, n_chains, n_levels, chain_len;
-  double fwd, Tmax;
-  std::vector<double> lfk, l2kf, l2k, T, mkt, mT, ck;
-  std::vector<int> mat;
-  double x0[kMaxD];
-  double lo[kMaxD], hi[kMaxD];
-  double T0, step0, step_min;
-  uint64_t seed;
-};
-
-static sabr_status prepare(const sabr_problem& pr, const sabr_bounds& b, const sabr_cooling& c,
-                           uint64_t seed, HostProblem& h) {
+sabr_status formula_prepare(const sabr_problem& pr, const sabr_bounds& b, const sabr_cooling& c, uint64_t seed,
+                            HostProblem& h) {
   h.model = pr.model;
   h.d = n_params(pr.model);
   if (h.d < 0) return fail(SABR_EINVAL, "unknown model");
-  if (pr.cost != SABR_COST_VOL && pr.cost != SABR_COST_MC_PRICE) return fail(SABR_EINVAL, "unknown cost");
-  if (pr.cost == SABR_COST_MC_PRICE) return fail(SABR_EINVAL, "MC-price cost is calibrated by the MC engine");
+  if (pr.cost != SABR_COST_VOL) return fail(SABR_EINVAL, "not an implied-vol cost");
   if (pr.prec != SABR_FP32 && pr.prec != SABR_FP64) return fail(SABR_EINVAL, "unknown precision");
   if (!(pr.fwd > 0.0) || !std::isfinite(pr.fwd)) return fail(SABR_EINVAL, "fwd must be > 0");
   if (pr.n_quotes < 1 || pr.n_quotes > kMaxQuotes) return fail(SABR_EINVAL, "n_quotes must lie in [1, 4096]");
   if (!pr.T || !pr.K || !pr.market) return fail(SABR_EINVAL, "NULL quote array");
   if (pr.n_chains < 1 || pr.n_chains > (1 << 24)) return fail(SABR_EINVAL, "n_chains must lie in [1, 2^24]");
-  if (!(c.factor > 0.0) || !std::isfinite(c.factor) || c.n_levels < 0 || c.chain_len < 0 ||
-      !(c.step0 >= 0.0) || !(c.step_min >= 0.0) || !std::isfinite(c.T0) || !std::isfinite(c.step0) ||
-      !std::isfinite(c.step_min))
+  if (!(c.factor > 0.0) || !std::isfinite(c.factor) || c.n_levels < 0 || c.chain_len < 0 || !(c.step0 >= 0.0) ||
+      !(c.step_min >= 0.0) || !std::isfinite(c.T0) || !std::isfinite(c.step0) || !std::isfinite(c.step_min))
     return fail(SABR_EINVAL, "bad cooling schedule");
   h.prec = pr.prec;
   h.cost = pr.cost;
@@ -628,6 +526,246 @@ static sabr_status prepare(const sabr_problem& pr, const sabr_bounds& b, const s
   return SABR_OK;
 }
 
+size_t formula_layout(const HostProblem& h, int G, unsigned char* img, unsigned char* base, size_t off0,
+                      ProblemDev& d, sabr_result* dres) {
+  size_t o = off0;
+  auto take = [&](size_t bytes) {
+    o = align_up(o, 256);
+    const size_t r = o;
+    o += bytes;
+    return r;
+  };
+  const bool write = img != nullptr;
+  auto put = [&](size_t at, const void* src, size_t bytes) {
+    if (write) std::memcpy(img + at, src, bytes);
+  };
+  std::memset(&d, 0, sizeof(d));
+  d.model = h.model;
+  d.prec = h.prec;
+  d.cost = h.cost;
+  d.d = h.d;
+  d.n_quotes = h.n_quotes;
+  d.n_mats = h.n_mats;
+  d.n_chains = h.n_chains;
+  d.n_levels = h.n_levels;
+  d.chain_len = h.chain_len;
+  d.G = G;
+  d.cpb = kSaBlock / G;
+  d.n_blocks = (h.n_chains + d.cpb - 1) / d.cpb;
+  d.fwd = h.fwd;
+  d.l2f = std::log2(h.fwd);
+  d.Tmax = h.Tmax;
+  for (int k = 0; k < kMaxD; ++k) {
+    d.lo[k] = h.lo[k];
+    d.hi[k] = h.hi[k];
+  }
+  d.T0_given = h.T0;
+  d.step0 = h.step0;
+  d.step_min = h.step_min;
+  d.key0 = (uint32_t)h.seed;
+  d.key1 = (uint32_t)(h.seed >> 32);
+  const size_t rs = h.prec == SABR_FP64 ? 8 : 4;
+  const size_t Q = h.n_quotes, M = h.n_mats, C = h.n_chains, B = d.n_blocks;
+  const size_t o_lfk = take(Q * rs), o_l2kf = take(Q * rs), o_l2k = take(Q * rs), o_T = take(Q * rs),
+               o_w = take(Q * rs), o_mat = take(Q * 4), o_mT = take(M * rs);
+  const size_t o64_lfk = take(Q * 8), o64_l2kf = take(Q * 8), o64_l2k = take(Q * 8), o64_T = take(Q * 8),
+               o64_mkt = take(Q * 8), o64_mT = take(M * 8);
+  const size_t o_ck = take(h.ck.size() * 8), o_x0 = take(kMaxD * 8), o_state = take(kStateLen * 8);
+  const size_t o_bf = take(C * 8), o_bx = take(C * kMaxD * rs), o_ev = take(C * 8), o_ac = take(C * 8);
+  const size_t o_pf = take(B * 8), o_pc = take(B * 4), o_px = take(B * kMaxD * 8), o_arr = take(4);
+  if (write) {
+    if (h.prec == SABR_FP64) {
+      put(o_lfk, h.lfk.data(), Q * 8);
+      put(o_l2kf, h.l2kf.data(), Q * 8);
+      put(o_l2k, h.l2k.data(), Q * 8);
+      put(o_T, h.T.data(), Q * 8);
+      put(o_w, h.mkt.data(), Q * 8);
+      put(o_mT, h.mT.data(), M * 8);
+    } else {
+      std::vector<float> t(Q);
+      for (size_t k = 0; k < Q; ++k) t[k] = (float)h.lfk[k];
+      put(o_lfk, t.data(), Q * 4);
+      for (size_t k = 0; k < Q; ++k) t[k] = (float)h.l2kf[k];
+      put(o_l2kf, t.data(), Q * 4);
+      for (size_t k = 0; k < Q; ++k) t[k] = (float)h.l2k[k];
+      put(o_l2k, t.data(), Q * 4);
+      for (size_t k = 0; k < Q; ++k) t[k] = (float)h.T[k];
+      put(o_T, t.data(), Q * 4);
+      for (size_t k = 0; k < Q; ++k) t[k] = (float)(1.0 / h.mkt[k]);
+      put(o_w, t.data(), Q * 4);
+      std::vector<float> tm(M);
+      for (size_t k = 0; k < M; ++k) tm[k] = (float)h.mT[k];
+      put(o_mT, tm.data(), M * 4);
+    }
+    put(o_mat, h.mat.data(), Q * 4);
+    put(o64_lfk, h.lfk.data(), Q * 8);
+    put(o64_l2kf, h.l2kf.data(), Q * 8);
+    put(o64_l2k, h.l2k.data(), Q * 8);
+    put(o64_T, h.T.data(), Q * 8);
+    put(o64_mkt, h.mkt.data(), Q * 8);
+    put(o64_mT, h.mT.data(), M * 8);
+    put(o_ck, h.ck.data(), h.ck.size() * 8);
+    put(o_x0, h.x0, kMaxD * 8);
+    std::memset(img + o_arr, 0, 4);
+  }
+  d.q_lfk = base + o_lfk;
+  d.q_l2kf = base + o_l2kf;
+  d.q_l2k = base + o_l2k;
+  d.q_T = base + o_T;
+  d.q_w = base + o_w;
+  d.q_mat = (const int*)(base + o_mat);
+  d.m_T = base + o_mT;
+  d.q64_lfk = (const double*)(base + o64_lfk);
+  d.q64_l2kf = (const double*)(base + o64_l2kf);
+  d.q64_l2k = (const double*)(base + o64_l2k);
+  d.q64_T = (const double*)(base + o64_T);
+  d.q64_mkt = (const double*)(base + o64_mkt);
+  d.m64_T = (const double*)(base + o64_mT);
+  d.ck = (const double*)(base + o_ck);
+  d.x0 = (const double*)(base + o_x0);
+  d.state = (double*)(base + o_state);
+  d.chain_bf = (double*)(base + o_bf);
+  d.chain_bx = base + o_bx;
+  d.chain_ev = (unsigned long long*)(base + o_ev);
+  d.chain_ac = (unsigned long long*)(base + o_ac);
+  d.part_f = (double*)(base + o_pf);
+  d.part_c = (int*)(base + o_pc);
+  d.part_x = (double*)(base + o_px);
+  d.arrive = (unsigned int*)(base + o_arr);
+  d.result = dres;
+  return o;
+}
+
+// ---- launch wrappers ------------------------------------------------------
+template <class R, int MODEL>
+static void set_smem_one(size_t bytes) {
+  cudaFuncSetAttribute(sa_level_kernel<R, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(sa_level_persistent<R, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(sa_init_kernel<R, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+#define SABR_DISPATCH(prec, model, CALL)                              \
+  do {                                                                \
+    if ((prec) == SABR_FP64) {                                        \
+      using R = double;                                               \
+      switch (model) {                                                \
+        case SABR_HAGAN: { constexpr int M = SABR_HAGAN; CALL; } break;       \
+        case SABR_OBLOJ: { constexpr int M = SABR_OBLOJ; CALL; } break;       \
+        case SABR_EXPANDED: { constexpr int M = SABR_EXPANDED; CALL; } break; \
+        case SABR_DYN_I: { constexpr int M = SABR_DYN_I; CALL; } break;       \
+        default: { constexpr int M = SABR_DYN_II; CALL; } break;              \
+      }                                                               \
+    } else {                                                          \
+      using R = float;                                                \
+      switch (model) {                                                \
+        case SABR_HAGAN: { constexpr int M = SABR_HAGAN; CALL; } break;       \
+        case SABR_OBLOJ: { constexpr int M = SABR_OBLOJ; CALL; } break;       \
+        case SABR_EXPANDED: { constexpr int M = SABR_EXPANDED; CALL; } break; \
+        case SABR_DYN_I: { constexpr int M = SABR_DYN_I; CALL; } break;       \
+        default: { constexpr int M = SABR_DYN_II; CALL; } break;              \
+      }                                                               \
+    }                                                                 \
+  } while (0)
+
+void set_engine_smem(int prec, int model, size_t bytes) { SABR_DISPATCH(prec, model, (set_smem_one<R, M>(bytes))); }
+
+void launch_init(int prec, int model, const ProblemDev* probs, const int* plist, int n, size_t smem, cudaStream_t s) {
+  SABR_DISPATCH(prec, model, (sa_init_kernel<R, M><<<n, 32, smem, s>>>(probs, plist)));
+}
+
+void launch_level(int prec, int model, const ProblemDev* probs, const int2* bmap, int blocks, int level, size_t smem,
+                  cudaStream_t s) {
+  SABR_DISPATCH(prec, model, (sa_level_kernel<R, M><<<blocks, kSaBlock, smem, s>>>(probs, bmap, level)));
+}
+
+void launch_persistent(int prec, int model, const ProblemDev* probs, const int4* work, const int* n_work, int grid,
+                       size_t smem, cudaStream_t s) {
+  SABR_DISPATCH(prec, model, (sa_level_persistent<R, M><<<grid, kSaBlock, smem, s>>>(probs, work, n_work)));
+}
+
+void launch_finalize(int prec, int model, const ProblemDev* probs, const int* plist, int n, cudaStream_t s) {
+  SABR_DISPATCH(prec, model, (sa_finalize_kernel<R, M><<<n, kSaBlock, 0, s>>>(probs, plist)));
+}
+
+int persistent_blocks_per_sm(int prec, int model, size_t smem) {
+  int nb = 1;
+  SABR_DISPATCH(prec, model,
+                (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sa_level_persistent<R, M>, kSaBlock, smem)));
+  return nb < 1 ? 1 : nb;
+}
+
+struct LaunchGroup {
+  int prec = 0, model = 0;
+  std::vector<int> problems;
+  int total_blocks = 0;
+  int max_levels = 0;
+  size_t smem_level = 0, smem_init = 0;
+  int2* d_bmap = nullptr;
+  int* d_plist = nullptr;
+};
+
+}  // namespace sabr
+
+struct sabr_plan {
+  int device = 0;
+  int n = 0;
+  void* arena = nullptr;
+  sabr::ProblemDev* d_probs = nullptr;
+  sabr_result* d_results = nullptr;
+  sabr_result* h_results = nullptr;
+  std::vector<sabr::LaunchGroup> groups;
+  int max_levels = 0;
+  bool use_graph = false;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t own_stream = nullptr;
+  cudaEvent_t ev_lv0 = nullptr, ev_lv1 = nullptr, ev_done = nullptr;
+  int64_t launches = 0;
+  int64_t level_launches = 0;
+  bool ran = false;
+  std::vector<sabr::McSaHost> mc;  // Technique II problems
+  std::vector<int> mc_index;       // their batch index
+};
+
+namespace sabr {
+
+// The whole calibration of a plan, enqueued on s.
+static sabr_status enqueue_plan(sabr_plan* p, cudaStream_t s, bool capturing) {
+  int64_t launches = 0, level_launches = 0;
+  for (auto& g : p->groups) {
+    launch_init(g.prec, g.model, p->d_probs, g.d_plist, (int)g.problems.size(), g.smem_init, s);
+    ++launches;
+  }
+  if (capturing)
+    SABR_CUDA(cudaEventRecordWithFlags(p->ev_lv0, s, cudaEventRecordExternal));
+  else
+    SABR_CUDA(cudaEventRecord(p->ev_lv0, s));
+  for (int lv = 0; lv < p->max_levels; ++lv)
+    for (auto& g : p->groups) {
+      if (lv >= g.max_levels) continue;
+      launch_level(g.prec, g.model, p->d_probs, g.d_bmap, g.total_blocks, lv, g.smem_level, s);
+      ++launches;
+      ++level_launches;
+    }
+  if (capturing)
+    SABR_CUDA(cudaEventRecordWithFlags(p->ev_lv1, s, cudaEventRecordExternal));
+  else
+    SABR_CUDA(cudaEventRecord(p->ev_lv1, s));
+  for (auto& g : p->groups) {
+    launch_finalize(g.prec, g.model, p->d_probs, g.d_plist, (int)g.problems.size(), s);
+    ++launches;
+  }
+  for (auto& m : p->mc) {
+    const int64_t k = mcsa_enqueue(m, s);
+    if (k < 0) return SABR_ECUDA;
+    launches += k;
+  }
+  SABR_CUDA(cudaGetLastError());
+  SABR_CUDA(cudaMemcpyAsync(p->h_results, p->d_results, sizeof(sabr_result) * p->n, cudaMemcpyDeviceToHost, s));
+  p->launches = launches;
+  p->level_launches = level_launches;
+  return SABR_OK;
+}
+
 static void free_plan(sabr_plan* p) {
   if (!p) return;
   if (p->exec) cudaGraphExecDestroy(p->exec);
@@ -641,89 +779,54 @@ static void free_plan(sabr_plan* p) {
 }
 
 static sabr_status build_plan(int32_t n, const sabr_problem* problems, const sabr_bounds* bounds,
-                              const sabr_cooling* cooling, const uint64_t* seeds, int use_graph,
-                              cudaStream_t stream, sabr_plan** out) {
+                              const sabr_cooling* cooling, const uint64_t* seeds, int use_graph, cudaStream_t stream,
+                              sabr_plan** out) {
   if (!out) return fail(SABR_EINVAL, "out is NULL");
   *out = nullptr;
   if (n < 1 || !problems || !bounds || !cooling || !seeds) return fail(SABR_EINVAL, "empty batch or NULL array");
-  std::vector<HostProblem> hp(n);
+  std::vector<HostProblem> hp;
+  std::vector<int> fidx, midx;
+  std::vector<McSaHost> mch;
   long long batch_chains = 0;
   for (int i = 0; i < n; ++i) {
-    SABR_TRY(prepare(problems[i], bounds[i], cooling[i], seeds[i], hp[i]));
-    batch_chains += hp[i].n_chains;
+    if (problems[i].cost == SABR_COST_MC_PRICE) {
+      mch.emplace_back();
+      SABR_TRY(mcsa_prepare(problems[i], bounds[i], cooling[i], seeds[i], mch.back()));
+      midx.push_back(i);
+    } else {
+      hp.emplace_back();
+      SABR_TRY(formula_prepare(problems[i], bounds[i], cooling[i], seeds[i], hp.back()));
+      batch_chains += hp.back().n_chains;
+      fidx.push_back(i);
+    }
   }
+  const int nf = (int)hp.size();
   sabr_plan* p = new sabr_plan();
   p->n = n;
+  p->mc_index = midx;
+  p->mc = std::move(mch);
   cudaGetDevice(&p->device);
 
-  // Arena layout.
-  Arena ar;
-  struct Off {
-    size_t lfk, l2kf, l2k, T, w, mat, mT, q64_lfk, q64_l2kf, q64_l2k, q64_T, q64_mkt, m64_T, ck, x0, state,
-        bf, bx, ev, ac, pf, pc, px, arrive;
+  // arena: problem table, results, per-problem regions, launch maps
+  std::vector<int> lanes(nf);
+  std::vector<ProblemDev> pd(nf);
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    o = align_up(o, 256);
+    const size_t r = o;
+    o += bytes;
+    return r;
   };
-  std::vector<Off> off(n);
-  std::vector<ProblemDev> pd(n);
-  size_t probs_off = ar.take(sizeof(ProblemDev) * n);
-  size_t results_off = ar.take(sizeof(sabr_result) * n);
-  for (int i = 0; i < n; ++i) {
-    HostProblem& h = hp[i];
-    ProblemDev& d = pd[i];
-    std::memset(&d, 0, sizeof(d));
-    d.model = h.model;
-    d.prec = h.prec;
-    d.cost = h.cost;
-    d.d = h.d;
-    d.n_quotes = h.n_quotes;
-    d.n_mats = h.n_mats;
-    d.n_chains = h.n_chains;
-    d.n_levels = h.n_levels;
-    d.chain_len = h.chain_len;
-    d.G = choose_lanes(h.n_quotes, h.n_mats, h.model, batch_chains);
-    d.cpb = kSaBlock / d.G;
-    d.n_blocks = (h.n_chains + d.cpb - 1) / d.cpb;
-    d.fwd = h.fwd;
-    d.l2f = std::log2(h.fwd);
-    d.Tmax = h.Tmax;
-    for (int k = 0; k < kMaxD; ++k) {
-      d.lo[k] = h.lo[k];
-      d.hi[k] = h.hi[k];
-    }
-    d.T0_given = h.T0;
-    d.step0 = h.step0;
-    d.step_min = h.step_min;
-    d.key0 = (uint32_t)h.seed;
-    d.key1 = (uint32_t)(h.seed >> 32);
-    const size_t rs = h.prec == SABR_FP64 ? 8 : 4;
-    const size_t Q = h.n_quotes, M = h.n_mats;
-    Off& o = off[i];
-    o.lfk = ar.take(Q * rs);
-    o.l2kf = ar.take(Q * rs);
-    o.l2k = ar.take(Q * rs);
-    o.T = ar.take(Q * rs);
-    o.w = ar.take(Q * rs);
-    o.mat = ar.take(Q * 4);
-    o.mT = ar.take(M * rs);
-    o.q64_lfk = ar.take(Q * 8);
-    o.q64_l2kf = ar.take(Q * 8);
-    o.q64_l2k = ar.take(Q * 8);
-    o.q64_T = ar.take(Q * 8);
-    o.q64_mkt = ar.take(Q * 8);
-    o.m64_T = ar.take(M * 8);
-    o.ck = ar.take(h.ck.size() * 8);
-    o.x0 = ar.take(kMaxD * 8);
-    o.state = ar.take(kStateLen * 8);
-    o.bf = ar.take((size_t)h.n_chains * 8);
-    o.bx = ar.take((size_t)h.n_chains * kMaxD * rs);
-    o.ev = ar.take((size_t)h.n_chains * 8);
-    o.ac = ar.take((size_t)h.n_chains * 8);
-    o.pf = ar.take((size_t)d.n_blocks * 8);
-    o.pc = ar.take((size_t)d.n_blocks * 4);
-    o.px = ar.take((size_t)d.n_blocks * kMaxD * 8);
-    o.arrive = ar.take(4);
+  const size_t probs_off = take(sizeof(ProblemDev) * std::max(nf, 1));
+  const size_t results_off = take(sizeof(sabr_result) * n);
+  std::vector<size_t> f_off(nf), mc_off(p->mc.size());
+  for (int i = 0; i < nf; ++i) {
+    lanes[i] = choose_lanes(hp[i].n_quotes, hp[i].n_mats, hp[i].model, batch_chains);
+    f_off[i] = align_up(o, 256);
+    o = formula_layout(hp[i], lanes[i], nullptr, nullptr, f_off[i], pd[i], nullptr);
   }
-  // launch groups: one per (precision, model)
-  for (int i = 0; i < n; ++i) {
+  for (size_t k = 0; k < p->mc.size(); ++k) mc_off[k] = take(mcsa_arena_bytes(p->mc[k]));
+  for (int i = 0; i < nf; ++i) {
     LaunchGroup* g = nullptr;
     for (auto& gg : p->groups)
       if (gg.prec == hp[i].prec && gg.model == hp[i].model) g = &gg;
@@ -736,106 +839,43 @@ static sabr_status build_plan(int32_t n, const sabr_problem* problems, const sab
     g->problems.push_back(i);
     g->total_blocks += pd[i].n_blocks;
     g->max_levels = std::max(g->max_levels, hp[i].n_levels);
-    g->smem_level = std::max(g->smem_level, level_smem_bytes(hp[i].prec, hp[i].n_quotes, hp[i].n_mats, pd[i].cpb));
-    g->smem_init = std::max(g->smem_init, level_smem_bytes(hp[i].prec, hp[i].n_quotes, hp[i].n_mats, 1));
+    g->smem_level = std::max(g->smem_level, level_smem_bytes(hp[i].prec, hp[i].model, hp[i].n_quotes, hp[i].n_mats,
+                                                              pd[i].cpb));
+    g->smem_init = std::max(g->smem_init, init_smem_bytes(hp[i]));
     p->max_levels = std::max(p->max_levels, hp[i].n_levels);
   }
   std::vector<size_t> bmap_off(p->groups.size()), plist_off(p->groups.size());
   for (size_t gi = 0; gi < p->groups.size(); ++gi) {
-    bmap_off[gi] = ar.take(sizeof(int2) * p->groups[gi].total_blocks);
-    plist_off[gi] = ar.take(sizeof(int) * p->groups[gi].problems.size());
+    bmap_off[gi] = take(sizeof(int2) * p->groups[gi].total_blocks);
+    plist_off[gi] = take(sizeof(int) * p->groups[gi].problems.size());
   }
+  const size_t arena_bytes = align_up(o, 256);
 
-  // Host image of the arena, then one copy.
-  std::vector<unsigned char> img(ar.size, 0);
-  cudaError_t e = cudaMalloc(&p->arena, ar.size);
+  std::vector<unsigned char> img(arena_bytes, 0);
+  cudaError_t e = cudaMalloc(&p->arena, arena_bytes);
   if (e != cudaSuccess) {
     free_plan(p);
     return cuda_fail(e, "cudaMalloc(plan arena)");
   }
   unsigned char* base = (unsigned char*)p->arena;
-  auto put = [&](size_t o, const void* src, size_t bytes) { std::memcpy(img.data() + o, src, bytes); };
-  for (int i = 0; i < n; ++i) {
-    HostProblem& h = hp[i];
-    ProblemDev& d = pd[i];
-    Off& o = off[i];
-    const int Q = h.n_quotes, M = h.n_mats;
-    if (h.prec == SABR_FP64) {
-      put(o.lfk, h.lfk.data(), Q * 8);
-      put(o.l2kf, h.l2kf.data(), Q * 8);
-      put(o.l2k, h.l2k.data(), Q * 8);
-      put(o.T, h.T.data(), Q * 8);
-      put(o.w, h.mkt.data(), Q * 8);
-      put(o.mT, h.mT.data(), M * 8);
-    } else {
-      std::vector<float> t(Q);
-      for (int k = 0; k < Q; ++k) t[k] = (float)h.lfk[k];
-      put(o.lfk, t.data(), Q * 4);
-      for (int k = 0; k < Q; ++k) t[k] = (float)h.l2kf[k];
-      put(o.l2kf, t.data(), Q * 4);
-      for (int k = 0; k < Q; ++k) t[k] = (float)h.l2k[k];
-      put(o.l2k, t.data(), Q * 4);
-      for (int k = 0; k < Q; ++k) t[k] = (float)h.T[k];
-      put(o.T, t.data(), Q * 4);
-      for (int k = 0; k < Q; ++k) t[k] = (float)(1.0 / h.mkt[k]);
-      put(o.w, t.data(), Q * 4);
-      std::vector<float> tm(M);
-      for (int k = 0; k < M; ++k) tm[k] = (float)h.mT[k];
-      put(o.mT, tm.data(), M * 4);
-    }
-    put(o.mat, h.mat.data(), Q * 4);
-    put(o.q64_lfk, h.lfk.data(), Q * 8);
-    put(o.q64_l2kf, h.l2kf.data(), Q * 8);
-    put(o.q64_l2k, h.l2k.data(), Q * 8);
-    put(o.q64_T, h.T.data(), Q * 8);
-    put(o.q64_mkt, h.mkt.data(), Q * 8);
-    put(o.m64_T, h.mT.data(), M * 8);
-    put(o.ck, h.ck.data(), h.ck.size() * 8);
-    put(o.x0, h.x0, kMaxD * 8);
-    d.q_lfk = base + o.lfk;
-    d.q_l2kf = base + o.l2kf;
-    d.q_l2k = base + o.l2k;
-    d.q_T = base + o.T;
-    d.q_w = base + o.w;
-    d.q_mat = (const int*)(base + o.mat);
-    d.m_T = base + o.mT;
-    d.q64_lfk = (const double*)(base + o.q64_lfk);
-    d.q64_l2kf = (const double*)(base + o.q64_l2kf);
-    d.q64_l2k = (const double*)(base + o.q64_l2k);
-    d.q64_T = (const double*)(base + o.q64_T);
-    d.q64_mkt = (const double*)(base + o.q64_mkt);
-    d.m64_T = (const double*)(base + o.m64_T);
-    d.ck = (const double*)(base + o.ck);
-    d.x0 = (const double*)(base + o.x0);
-    d.state = (double*)(base + o.state);
-    d.chain_bf = (double*)(base + o.bf);
-    d.chain_bx = base + o.bx;
-    d.chain_ev = (unsigned long long*)(base + o.ev);
-    d.chain_ac = (unsigned long long*)(base + o.ac);
-    d.part_f = (double*)(base + o.pf);
-    d.part_c = (int*)(base + o.pc);
-    d.part_x = (double*)(base + o.px);
-    d.arrive = (unsigned int*)(base + o.arrive);
-    d.result = (sabr_result*)(base + results_off) + i;
-  }
-  put(probs_off, pd.data(), sizeof(ProblemDev) * n);
+  sabr_result* dres = (sabr_result*)(base + results_off);
+  for (int i = 0; i < nf; ++i) formula_layout(hp[i], lanes[i], img.data(), base, f_off[i], pd[i], dres + fidx[i]);
+  for (size_t k = 0; k < p->mc.size(); ++k) mcsa_layout(p->mc[k], img.data(), base, mc_off[k], dres + p->mc_index[k]);
+  if (nf > 0) std::memcpy(img.data() + probs_off, pd.data(), sizeof(ProblemDev) * nf);
   for (size_t gi = 0; gi < p->groups.size(); ++gi) {
     LaunchGroup& g = p->groups[gi];
     std::vector<int2> bm;
     for (int pi : g.problems)
       for (int b = 0; b < pd[pi].n_blocks; ++b) bm.push_back(make_int2(pi, b));
-    put(bmap_off[gi], bm.data(), sizeof(int2) * bm.size());
-    put(plist_off[gi], g.problems.data(), sizeof(int) * g.problems.size());
+    std::memcpy(img.data() + bmap_off[gi], bm.data(), sizeof(int2) * bm.size());
+    std::memcpy(img.data() + plist_off[gi], g.problems.data(), sizeof(int) * g.problems.size());
     g.d_bmap = (int2*)(base + bmap_off[gi]);
     g.d_plist = (int*)(base + plist_off[gi]);
-    if (g.prec == SABR_FP64)
-      set_smem_attr_model<double>(g.model, std::max(g.smem_level, g.smem_init));
-    else
-      set_smem_attr_model<float>(g.model, std::max(g.smem_level, g.smem_init));
+    set_engine_smem(g.prec, g.model, std::max(g.smem_level, g.smem_init));
   }
   p->d_probs = (ProblemDev*)(base + probs_off);
-  p->d_results = (sabr_result*)(base + results_off);
-  e = cudaMemcpy(p->arena, img.data(), ar.size, cudaMemcpyHostToDevice);
+  p->d_results = dres;
+  e = cudaMemcpy(p->arena, img.data(), arena_bytes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMallocHost(&p->h_results, sizeof(sabr_result) * n);
   if (e == cudaSuccess) e = cudaEventCreate(&p->ev_lv0);
   if (e == cudaSuccess) e = cudaEventCreate(&p->ev_lv1);
@@ -902,8 +942,8 @@ static sabr_status plan_results(sabr_plan* p, sabr_result* out) {
 extern "C" {
 
 sabr_status sabr_plan_create(int32_t n, const sabr_problem* problems, const sabr_bounds* bounds,
-                             const sabr_cooling* cooling, const uint64_t* seeds, int32_t use_graph,
-                             void* stream, sabr_plan** out) {
+                             const sabr_cooling* cooling, const uint64_t* seeds, int32_t use_graph, void* stream,
+                             sabr_plan** out) {
   sabr::clear_error();
   return sabr::build_plan(n, problems, bounds, cooling, seeds, use_graph, (cudaStream_t)stream, out);
 }
@@ -939,8 +979,7 @@ sabr_status sabr_plan_stats(sabr_plan* plan, int64_t* launches, double* level_ms
 void sabr_plan_destroy(sabr_plan* plan) { sabr::free_plan(plan); }
 
 sabr_status sabr_calibrate_batch(int32_t n, const sabr_problem* problems, const sabr_bounds* bounds,
-                                 const sabr_cooling* cooling, const uint64_t* seeds, sabr_result* out,
-                                 void* stream) {
+                                 const sabr_cooling* cooling, const uint64_t* seeds, sabr_result* out, void* stream) {
   sabr::clear_error();
   if (!out) return sabr::fail(SABR_EINVAL, "out is NULL");
   sabr_plan* p = nullptr;
@@ -951,8 +990,8 @@ sabr_status sabr_calibrate_batch(int32_t n, const sabr_problem* problems, const 
   return st;
 }
 
-sabr_status sabr_calibrate(const sabr_problem* problem, const sabr_bounds* bounds,
-                           const sabr_cooling* cooling, uint64_t seed, sabr_result* out, void* stream) {
+sabr_status sabr_calibrate(const sabr_problem* problem, const sabr_bounds* bounds, const sabr_cooling* cooling,
+                           uint64_t seed, sabr_result* out, void* stream) {
   return sabr_calibrate_batch(1, problem, bounds, cooling, &seed, out, stream);
 }
 

@@ -1,0 +1,49 @@
+"""GPU parity of Technique II (Sec. 5.2): SA whose cost is the misfit of
+Monte Carlo prices on common random numbers, against the oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2407_20713_gb300 as sg
+
+pytestmark = pytest.mark.gpu
+
+T = np.array([0.5, 0.5, 1.0, 1.0, 1.5])
+K = np.array([0.9, 1.1, 0.9, 1.1, 1.0])
+
+
+def _problem(model, lo, hi, prec, truth, **kw):
+    mkt, _ = O.mc_price(model, truth, 1.0, T, K, n_paths=8192, steps_per_year=50, seed=77)
+    pb = sg.CalibrationProblem(model=model, T=T, K=K, market=mkt, lo=lo, hi=hi, prec=prec, cost=sg.COST_MC_PRICE,
+                               mc_paths=2048, mc_steps_per_year=50, mc_seed=5, **kw)
+    return pb, mkt
+
+
+@pytest.mark.parametrize("model,truth,lo,hi", [
+    (sg.HAGAN, [0.25, 0.6, -0.3, 0.5], [0.25, 0.6, -0.9, 0.1], [0.25, 0.6, 0.5, 1.5]),
+    (sg.DYN_I, [0.25, 0.8, -0.4, 0.6, 0.5, 0.8], [0.1, 0.8, -0.9, 0.1, 0.0, 0.0], [0.5, 0.8, 0.5, 1.5, 2.0, 2.0]),
+])
+def test_fp64_mc_cost_trajectory_is_the_oracle_trajectory(model, truth, lo, hi):
+    pb, mkt = _problem(model, lo, hi, sg.FP64, truth, n_chains=6, n_levels=3, chain_len=4, seed=9)
+    g = sg.calibrate(pb)
+    o = O.sa_calibrate(model, 1.0, T, K, mkt, lo, hi, cost=O.COST_MC, n_chains=6, n_levels=3, chain_len=4,
+                       mc_paths=2048, mc_steps_per_year=50, mc_seed=5, seed=9, n_threads=8)
+    assert g.status == 0
+    assert g.n_evals == o["n_evals"] and g.n_accepts == o["n_accepts"]
+    np.testing.assert_allclose(g.params, o["params"], rtol=1e-9, atol=1e-13)
+    assert g.misfit == pytest.approx(o["misfit"], rel=1e-8)
+    assert g.misfit_fp64 == pytest.approx(o["misfit"], rel=1e-8)
+
+
+def test_fp32_mc_cost_stays_close_to_the_oracle():
+    truth = [0.25, 0.6, -0.3, 0.5]
+    lo, hi = [0.25, 0.6, -0.9, 0.1], [0.25, 0.6, 0.5, 1.5]
+    pb, mkt = _problem(sg.HAGAN, lo, hi, sg.FP32, truth, n_chains=16, n_levels=6, chain_len=6, seed=3)
+    g = sg.calibrate(pb)
+    o = O.sa_calibrate(sg.HAGAN, 1.0, T, K, mkt, lo, hi, cost=O.COST_MC, n_chains=16, n_levels=6, chain_len=6,
+                       mc_paths=2048, mc_steps_per_year=50, mc_seed=5, seed=3, n_threads=8)
+    assert g.status == 0
+    # FP32 prices move the misfit by ~1e-5 relative per quote; trajectories may
+    # part ways late, so compare outcomes: both reach the same basin.
+    assert abs(g.misfit_fp64 - o["misfit"]) <= 0.5 * o["misfit"] + 1e-6
+    np.testing.assert_allclose(g.params[2:], o["params"][2:], atol=0.1)
