@@ -237,7 +237,7 @@ double orc_nu_t(int dyn_case, const double* p, double t) {
   return (p[3] + p[9] * t) * exp(-p[5] * t) + p[7];
 }
 
-typedef struct { int dyn_case; const double* p; double T; } dyn_ctx;
+typedef struct { int dyn_case; const double* p; double T; int npan; } dyn_ctx;
 
 static double ig_nu1(double t, void* v) { /* (T-t)^2 nu(t)^2 */
   const dyn_ctx* c = (const dyn_ctx*)v;
@@ -257,17 +257,48 @@ static double ig_eta1(double t, void* v) { /* (T-t) nu(t) rho(t) */
   const dyn_ctx* c = (const dyn_ctx*)v;
   return (c->T - t) * ig_nurho(t, v);
 }
+/* G(s) = int_0^s nu(u) rho(u) du by the composite 10-point rule on c->npan
+ * equal panels of [0, s].  A fixed rule makes G a smooth function of s, so
+ * the outer adaptive integral below converges (an adaptive inner rule would
+ * change its subdivision with s and leave non-smooth rounding noise). */
+static double G_fixed(const dyn_ctx* c, double s, double* absint) {
+  const double h = s / c->npan;
+  double g = 0.0, a = 0.0;
+  for (int k = 0; k < c->npan; ++k) {
+    double ak;
+    g += gl10(ig_nurho, (void*)c, k * h, (k + 1) * h, &ak);
+    a += ak;
+  }
+  if (absint) *absint = a;
+  return g;
+}
+
+/* Panels for G_fixed: the fewest (a power of two) for which doubling them
+ * changes G(T) by no more than 1e-15 of int_0^T |nu rho|. */
+static int choose_panels(dyn_ctx* c) {
+  c->npan = 1;
+  double a, g = G_fixed(c, c->T, &a);
+  for (int n = 2; n <= (1 << 16); n *= 2) {
+    c->npan = n;
+    double a2, g2 = G_fixed(c, c->T, &a2);
+    if (fabs(g2 - g) <= 1e-15 * a2 + 1e-300) return n;
+    g = g2;
+  }
+  return c->npan;
+}
+
 /* eta2^2 = (12/T^4) int_0^T int_0^t G(s)^2 ds dt with G(s) = int_0^s nu rho.
  * Exchanging the order of the two outer integrals over 0 <= s <= t <= T
- * (Fubini) gives (12/T^4) int_0^T (T - s) G(s)^2 ds; G by inner quadrature. */
+ * (Fubini) gives (12/T^4) int_0^T (T - s) G(s)^2 ds. */
 static double ig_eta2(double s, void* v) {
   const dyn_ctx* c = (const dyn_ctx*)v;
-  double G = orc_integrate(ig_nurho, v, 0.0, s, 1e-15);
+  double G = G_fixed(c, s, NULL);
   return (c->T - s) * G * G;
 }
 
 void orc_dyn_coeffs(int dyn_case, const double* p, double T, double out[4]) {
-  dyn_ctx c = {dyn_case, p, T};
+  dyn_ctx c = {dyn_case, p, T, 1};
+  choose_panels(&c);
   double T2 = T * T, T3 = T2 * T, T4 = T3 * T;
   out[0] = 3.0 / T3 * orc_integrate(ig_nu1, &c, 0.0, T, 1e-15);
   out[1] = 6.0 / T3 * orc_integrate(ig_nu2, &c, 0.0, T, 1e-15);
