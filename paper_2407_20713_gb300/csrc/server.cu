@@ -484,6 +484,9 @@ static sabr_status submit(sabr_server* s, const sabr_problem* pr, const sabr_bou
     r->bytes = formula_layout(r->hp, r->G, nullptr, nullptr, 0, tmp, nullptr) + 256;
     r->n_blocks = tmp.n_blocks;
     if (r->n_blocks > kWorkPerGroup) return fail(SABR_EINVAL, "request has too many chains for one step");
+    const size_t need = level_smem_bytes(r->hp.prec, r->hp.model, r->hp.n_quotes, r->hp.n_mats, tmp.cpb);
+    if (need > s->smem[group_of(r->hp.prec, r->hp.model)])
+      return fail(SABR_EINVAL, "request needs more shared memory than the server reserves");
   }
   if (r->bytes > (size_t)s->cfg.device_bytes) return fail(SABR_EINVAL, "request larger than the server pool");
   std::lock_guard<std::mutex> lk(s->mu);
