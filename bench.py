@@ -43,6 +43,11 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 form")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-extra", action="store_true", help="skip the MC, dynamic and serving measurements")
+    ap.add_argument("--case", choices=["full", "small", "mc"], default="full",
+                    help="small: 2 smiles x 10 levels, main measurement only; mc: one 2^20-path MC pricing "
+                         "of the MC surface (both for profiler captures)")
+    ap.add_argument("--serve-requests", type=int, default=400)
     return ap.parse_args()
 
 
@@ -156,6 +161,169 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+
+def grid_steps(maturities, spy):
+    """Number of steps of the MC time grid (every multiple of 1/spy below the
+    last maturity, with each maturity inserted)."""
+    mats = sorted(set(float(t) for t in maturities))
+    n, k = 0, 1
+    for Tm in mats:
+        while k / spy < Tm - 1e-10:
+            n += 1
+            k += 1
+        n += 1
+        if abs(k / spy - Tm) <= 1e-10:
+            k += 1
+    return n
+
+
+def measure_mc(sg, torch, stream, rates, sm_mhz):
+    """sabr_mc_price on the Monte Carlo surface shape: 8 maturities x 15
+    strikes of calls, 2^22 paths, 250 steps a year (504 grid steps)."""
+    from paper_2407_20713_gb300 import workloads
+    w = workloads.mc_surface()
+    n_paths = 1 << 22
+    steps = grid_steps(w.T, 250.0)
+    out = {}
+    for prec, name in ((sg.FP32, "fp32"), (sg.FP64, "fp64")):
+        sg.mc_price(sg.HAGAN, w.truth, 1.0, w.T, w.K, n_paths=1 << 16, steps_per_year=250, seed=1, prec=prec)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sg.mc_price(sg.HAGAN, w.truth, 1.0, w.T, w.K, n_paths=n_paths, steps_per_year=250, seed=1, prec=prec)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        out[name] = {"value": n_paths * steps / (ms / 1e3), "unit": "path-steps/s", "ms": ms}
+    res = {"workload": "8 maturities x 15 strikes, 2^22 paths, %d steps, Hagan dynamics" % steps,
+           "value": out["fp32"]["value"], "unit": "path-steps/s", "fp64_form": out["fp64"]}
+    if rates:
+        sfu = min(rates[1], rates[3], rates[4])
+        peak = SMS * sfu * sm_mhz * 1e6 / 5.0
+        res["roofline"] = {"bound": "alu", "pipe": "SFU (log, sqrt, sin, cos of Box-Muller; exp of nu-hat): 5 per "
+                                                   "path-step", "achieved": res["value"], "peak": peak,
+                           "unit": "path-steps/s", "frac": res["value"] / peak}
+    return res
+
+
+def measure_dynamic(sg, torch, stream, levels=10):
+    """Joint dynamic fits on 12 maturities x 21 strikes, 8192 chains each, one
+    Case I and one Case II surface, FP32; `levels` of the 200 levels."""
+    import oracle  # noqa: F401  (not used: market vols come from the library)
+    from paper_2407_20713_gb300 import workloads
+    res = {}
+    for case, model in ((1, sg.DYN_I), (2, sg.DYN_II)):
+        w = workloads.dynamic_surface(case=case)
+        mkt = sg.implied_vol(model, w.truth, 1.0, w.T, w.K, prec=sg.FP64).cpu().numpy() + w.noise
+        pb = sg.CalibrationProblem(model=model, T=w.T, K=w.K, market=mkt, lo=w.lo, hi=w.hi, prec=sg.FP32,
+                                   n_chains=w.n_chains, n_levels=levels, chain_len=CHAIN_LEN, seed=3)
+        plan = sg.Plan([pb], use_graph=True)
+        plan.run(stream)
+        plan.results()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan.run(stream)
+        b.record(stream)
+        r = plan.results()[0]
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        res["case%d" % case] = {"value": r.n_evals / (ms / 1e3), "unit": "cost-evals/s", "ms": ms,
+                                "levels": levels, "quote_evals_per_s": r.n_evals * 252 / (ms / 1e3)}
+        plan.close()
+    return res
+
+
+def measure_serving(sg, n_requests, rate_hz):
+    """Poisson stream of calibration requests of uneven size (1-12 maturities x
+    5-41 strikes; 80% Hagan / 20% dynamic, 5% MC) through the server."""
+    import threading
+    from paper_2407_20713_gb300 import workloads
+    reqs = workloads.serving_stream(n=n_requests, rate_hz=rate_hz)
+    probs = []
+    for q in reqs:
+        sm = q.smile
+        if q.cost == 0:
+            mkt = sg.implied_vol(sm.model, sm.truth, 1.0, sm.T, sm.K, prec=sg.FP64).cpu().numpy() + sm.noise
+        else:
+            mkt = sg.mc_price(sm.model, sm.truth, 1.0, sm.T, sm.K, n_paths=q.mc_paths, steps_per_year=250,
+                              seed=99)[0].cpu().numpy()
+        probs.append(sg.CalibrationProblem(model=sm.model, T=sm.T, K=sm.K, market=mkt, lo=sm.lo, hi=sm.hi,
+                                           cost=q.cost, prec=sg.FP32, n_chains=sm.n_chains, n_levels=q.n_levels,
+                                           chain_len=q.chain_len, mc_paths=max(q.mc_paths, 2),
+                                           mc_steps_per_year=250.0, mc_seed=7, seed=11))
+    srv = sg.Server(device_bytes=8 << 30, max_active=512, max_quotes=512)
+    arrive, done, tickets = {}, {}, {}
+    lock = threading.Lock()
+    t0 = time.perf_counter()
+
+    def submitter():
+        for i, q in enumerate(reqs):
+            now = time.perf_counter() - t0
+            if q.arrival > now:
+                time.sleep(q.arrival - now)
+            a = time.perf_counter()
+            t = srv.submit(probs[i])
+            with lock:
+                arrive[i] = a
+                tickets[i] = t
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    deadline = time.perf_counter() + 600.0
+    while len(done) < len(reqs) and time.perf_counter() < deadline:
+        with lock:
+            outstanding = [(i, t) for i, t in tickets.items() if i not in done]
+        for i, t in outstanding:
+            if srv.poll(t) is not None:
+                done[i] = time.perf_counter()
+        time.sleep(0.0005)
+    th.join()
+    lat = np.array([done[i] - arrive[i] for i in done])
+    wall = max(done.values()) - t0
+    st = srv.stats()
+    srv.close()
+    return {"requests": len(reqs), "completed": len(done), "offered_rate_hz": rate_hz,
+            "calibrations_per_s": len(done) / wall,
+            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "steps": st["steps"], "kernel_launches": st["kernel_launches"], "wall_s": wall}
+
+def measure_serving_loads(sg, n_requests):
+    """Capacity (all requests at once), then Poisson arrivals at 80% of it;
+    beside it the plain FP64 one-request-per-launch form on a sample."""
+    burst = measure_serving(sg, n_requests, rate_hz=1e9)
+    cap = burst["calibrations_per_s"]
+    at80 = measure_serving(sg, n_requests, rate_hz=0.8 * cap)
+    from paper_2407_20713_gb300 import workloads
+    sample = workloads.serving_stream(n=24, rate_hz=1.0)
+    t0 = time.perf_counter()
+    n = 0
+    for q in sample:
+        if q.cost != 0:
+            continue
+        sm = q.smile
+        mkt = sg.implied_vol(sm.model, sm.truth, 1.0, sm.T, sm.K, prec=sg.FP64).cpu().numpy() + sm.noise
+        sg.calibrate(sg.CalibrationProblem(model=sm.model, T=sm.T, K=sm.K, market=mkt, lo=sm.lo, hi=sm.hi,
+                                           prec=sg.FP64, n_chains=sm.n_chains, n_levels=q.n_levels,
+                                           chain_len=q.chain_len, seed=11))
+        n += 1
+    fp64_rate = n / (time.perf_counter() - t0)
+    return {"capacity": burst, "load80": at80,
+            "fp64_one_request_per_launch": {"calibrations_per_s": fp64_rate, "sample": "%d formula requests" % n}}
+
+
+def run_mc_case():
+    """One sabr_mc_price on the MC surface shape at 2^20 paths (profiling)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2407_20713_gb300 as sg
+    from paper_2407_20713_gb300 import workloads
+    w = workloads.mc_surface()
+    for prec in (sg.FP32, sg.FP32, sg.FP64):
+        sg.mc_price(sg.HAGAN, w.truth, 1.0, w.T, w.K, n_paths=1 << 20, steps_per_year=250, seed=1, prec=prec)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "mc", "ok": True}))
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -172,6 +340,10 @@ def run_ours(args):
     from paper_2407_20713_gb300 import workloads
 
     smiles = workloads.static_surface(seed=20240721 + 1000 * rank, n_chains=N_CHAINS)
+    if args.case == "small":
+        global N_LEVELS
+        smiles = smiles[:2]
+        N_LEVELS = 10
     # market vols from the true parameters (library, FP64) plus seeded noise
     market = [sg.implied_vol(sg.HAGAN, sm.truth, 1.0, sm.T, sm.K, prec=sg.FP64).cpu().numpy() + sm.noise
               for sm in smiles]
@@ -273,7 +445,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": res_bytes},
             "roofline": roofline}
 
-    if not args.no_fp64:
+    if not args.no_fp64 and args.case == "full":
         p64 = sg.Plan(surface_problems(smiles, market, sg.FP64, seed0=7 + 100 * rank), use_graph=True)
         p64.run(stream)
         p64.results()
@@ -294,7 +466,15 @@ def run_ours(args):
     line["fp32_vs_fp64_misfit_rel_err_max"] = float(np.max(errs))
     plan.close()
 
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and not args.no_extra and args.case == "full":
+        for key, fn in (("mc", lambda: measure_mc(sg, torch, stream, rates, sm_mhz)),
+                        ("dynamic", lambda: measure_dynamic(sg, torch, stream)),
+                        ("serving", lambda: measure_serving_loads(sg, args.serve_requests))):
+            try:
+                line[key] = fn()
+            except Exception as exc:  # report, keep the headline line
+                line[key] = {"error": repr(exc)}
+    if rank == 0 and not args.no_cpu and args.case == "full":
         line["cpu_baseline"] = cpu_baseline(smiles, market)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -307,5 +487,7 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.case == "mc":
+        run_mc_case()
     else:
         run_ours(a)

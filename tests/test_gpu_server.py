@@ -81,14 +81,19 @@ def test_results_are_the_same_alone_and_in_the_mix(use_graph):
 
 def test_late_arrivals_join_running_requests():
     srv = sg.Server(device_bytes=256 << 20)
-    long_t = srv.submit(formula_request(1, n_chains=2048, n_levels=60, chain_len=50))
-    time.sleep(0.05)
+    # a request long enough to be resident for seconds
+    long_t = srv.submit(formula_request(1, n_chains=16384, n_levels=4000, chain_len=200))
+    time.sleep(0.1)
     short_t = srv.submit(formula_request(2, n_chains=64, n_levels=3, chain_len=5))
     short = srv.wait(short_t, timeout_ms=60000)
     # the short request finished while the long one was still resident
-    assert srv.poll(long_t) is None
     assert short.status == 0
-    srv.wait(long_t, timeout_ms=120000)
+    assert srv.poll(long_t) is None
+    assert srv.stats()["active"] >= 1
+    srv.cancel(long_t)
+    with pytest.raises(sg.SabrError) as e:
+        srv.wait(long_t, timeout_ms=120000)
+    assert e.value.status == sg.capi.ECANCELLED
     srv.close()
 
 
@@ -110,7 +115,7 @@ def test_admission_respects_the_device_pool():
 
 def test_host_side_limits_and_status_codes():
     srv = sg.Server(device_bytes=64 << 20, max_queue=2, max_active=1)
-    t1 = srv.submit(formula_request(6, n_chains=2048, n_levels=80, chain_len=50))
+    t1 = srv.submit(formula_request(6, n_chains=16384, n_levels=4000, chain_len=200))
     time.sleep(0.05)
     t2 = srv.submit(formula_request(7))
     t3 = srv.submit(formula_request(8))
