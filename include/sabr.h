@@ -109,6 +109,39 @@ sabr_status sabr_mc_price(sabr_model model, const double* params, double fwd,
                           sabr_precision prec, void* cuda_stream);
 
 /* ------------------------------------------------------------------------
+ * sabr_mc_price_noalloc -- the same prices as sabr_mc_price, for callers
+ * that cannot allocate memory while they run: code recording a CUDA graph
+ * around its own launches, processes whose device memory belongs to a
+ * custom or fixed-size allocator, latency-critical paths that must not hit
+ * the implicit synchronisation of cudaMalloc.  The paper has no counterpart;
+ * this is a deployment variant of the Sec. 4 pricer.
+ * Same arguments, layout and semantics as sabr_mc_price, with these
+ * differences:
+ *  - No cudaMalloc / cudaFree / cudaMallocHost / stream-ordered allocation
+ *    is made.  Scratch is one fixed 8 MiB device array in the library image
+ *    (every GPU that loads the library holds it until exit); host staging is
+ *    static storage.  Host arrays are copied with ordinary pageable copies.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture on the device.
+ *  - EINVAL when a problem needs more than the 8 MiB scratch -- per-block
+ *    partial sums take 256 B per block for every 16 options of a maturity
+ *    (up to 1216 blocks), and the option and time-step tables must fit in
+ *    256 KiB -- use sabr_mc_price then.
+ *  - All calls share the scratch and it keeps the last call's contents; each
+ *    call overwrites everything it reads.  Calls whose GPU work overlaps (on
+ *    different streams, or from threads with no ordering) race on it: order
+ *    them on one stream.
+ * ------------------------------------------------------------------------ */
+sabr_status sabr_mc_price_noalloc(sabr_model model, const double* params,
+                                  double fwd, const double* T, const double* K,
+                                  const int8_t* is_call, const double* discount,
+                                  int64_t n, int64_t n_paths,
+                                  double steps_per_year, uint64_t seed,
+                                  double* price_out, double* stderr_out,
+                                  sabr_precision prec, void* cuda_stream);
+
+/* ------------------------------------------------------------------------
  * Calibration problems (Sec. 3 eqs. (error_calibrate_individual_relativo),
  * (error_calibrate_relativo); Sec. 5).  All arrays in a problem are HOST
  * memory and are copied by the call that receives them.
