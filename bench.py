@@ -30,9 +30,26 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_LEVELS, CHAIN_LEN, N_CHAINS, FACTOR = 200, 100, 4096, 0.95
-SFU_PER_QUOTE = 5    # Hagan quote: (Kf)^((1-b)/2), sqrt, log, two divisions
-FP32_PER_QUOTE = 25  # the remaining FP32 arithmetic of eq. (haganf) + misfit
+# Algorithmic work of one Hagan quote evaluation (eq. haganf + the misfit
+# term), by pipe: one power (exp2 of a precomputed log), one square root, one
+# logarithm, two divisions, and about 25 FP32 adds/multiplies.
+HAGAN_QUOTE_OPS = {"ex2": 1, "rsq": 1, "lg2": 1, "rcp": 2, "fp32": 25}
+# One log-Euler path-step: Box-Muller (log, sqrt, sin, cos), the exp of
+# nu-hat, ~12 FP32 operations, and half a Philox4x32-10 block (ten rounds of
+# two 32x32 multiplies, each a low and a high half: 20 integer multiplies).
+MC_STEP_OPS = {"lg2": 1, "rsq": 1, "sin": 2, "ex2": 1, "fp32": 12, "imad": 20}
 SMS = 152
+
+
+def pipe_bound(ops, rates, sm_mhz):
+    """Units per second allowed by the busiest pipe: rates are operations per
+    SM clock (sabr_probe_pipe_rates: fma, ex2, lg2, rsq, rcp, sin, imad, dfma)."""
+    r = {"fp32": rates[0], "ex2": rates[1], "lg2": rates[2], "rsq": rates[3], "rcp": rates[4], "sin": rates[5],
+         "imad": rates[6]}
+    sfu = sum(n / r[k] for k, n in ops.items() if k in ("ex2", "lg2", "rsq", "rcp", "sin"))
+    t = {"sfu": sfu, "fp32": ops.get("fp32", 0) / r["fp32"], "int": ops.get("imad", 0) / r["imad"]}
+    pipe = max(t, key=t.get)
+    return SMS * sm_mhz * 1e6 / t[pipe], pipe, t
 
 
 def parse():
@@ -197,11 +214,10 @@ def measure_mc(sg, torch, stream, rates, sm_mhz):
     res = {"workload": "8 maturities x 15 strikes, 2^22 paths, %d steps, Hagan dynamics" % steps,
            "value": out["fp32"]["value"], "unit": "path-steps/s", "fp64_form": out["fp64"]}
     if rates:
-        sfu = min(rates[1], rates[3], rates[4])
-        peak = SMS * sfu * sm_mhz * 1e6 / 5.0
-        res["roofline"] = {"bound": "alu", "pipe": "SFU (log, sqrt, sin, cos of Box-Muller; exp of nu-hat): 5 per "
-                                                   "path-step", "achieved": res["value"], "peak": peak,
-                           "unit": "path-steps/s", "frac": res["value"] / peak}
+        peak, pipe, _ = pipe_bound(MC_STEP_OPS, rates, sm_mhz)
+        res["roofline"] = {"bound": "alu", "pipe": pipe, "ops_per_path_step": MC_STEP_OPS,
+                           "achieved": res["value"], "peak": peak, "unit": "path-steps/s",
+                           "frac": res["value"] / peak}
     return res
 
 
@@ -246,6 +262,9 @@ def measure_serving(sg, n_requests, rate_hz):
         else:
             mkt = sg.mc_price(sm.model, sm.truth, 1.0, sm.T, sm.K, n_paths=q.mc_paths, steps_per_year=250,
                               seed=99)[0].cpu().numpy()
+            # quotes priced below 1e-6 f are left out of a price calibration
+            keep = mkt >= 1e-6
+            sm.T, sm.K, mkt = sm.T[keep], sm.K[keep], mkt[keep]
         probs.append(sg.CalibrationProblem(model=sm.model, T=sm.T, K=sm.K, market=mkt, lo=sm.lo, hi=sm.hi,
                                            cost=q.cost, prec=sg.FP32, n_chains=sm.n_chains, n_levels=q.n_levels,
                                            chain_len=q.chain_len, mc_paths=max(q.mc_paths, 2),
@@ -255,21 +274,26 @@ def measure_serving(sg, n_requests, rate_hz):
     lock = threading.Lock()
     t0 = time.perf_counter()
 
+    errors = []
+
     def submitter():
-        for i, q in enumerate(reqs):
-            now = time.perf_counter() - t0
-            if q.arrival > now:
-                time.sleep(q.arrival - now)
-            a = time.perf_counter()
-            t = srv.submit(probs[i])
-            with lock:
-                arrive[i] = a
-                tickets[i] = t
+        try:
+            for i, q in enumerate(reqs):
+                now = time.perf_counter() - t0
+                if q.arrival > now:
+                    time.sleep(q.arrival - now)
+                a = time.perf_counter()
+                t = srv.submit(probs[i])
+                with lock:
+                    arrive[i] = a
+                    tickets[i] = t
+        except Exception as exc:  # surfaced below instead of stalling the poll loop
+            errors.append(exc)
 
     th = threading.Thread(target=submitter)
     th.start()
     deadline = time.perf_counter() + 600.0
-    while len(done) < len(reqs) and time.perf_counter() < deadline:
+    while len(done) < len(reqs) and time.perf_counter() < deadline and not errors:
         with lock:
             outstanding = [(i, t) for i, t in tickets.items() if i not in done]
         for i, t in outstanding:
@@ -277,6 +301,9 @@ def measure_serving(sg, n_requests, rate_hz):
                 done[i] = time.perf_counter()
         time.sleep(0.0005)
     th.join()
+    if errors:
+        srv.close()
+        raise errors[0]
     lat = np.array([done[i] - arrive[i] for i in done])
     wall = max(done.values()) - t0
     st = srv.stats()
@@ -322,6 +349,21 @@ def run_mc_case():
         sg.mc_price(sg.HAGAN, w.truth, 1.0, w.T, w.K, n_paths=1 << 20, steps_per_year=250, seed=1, prec=prec)
     torch.cuda.synchronize()
     print(json.dumps({"case": "mc", "ok": True}))
+
+
+def aggregate(t_local, units_local, e2e_local, dist=None):
+    """Whole-job numbers across ranks: time = max over ranks (all ranks start
+    together after a barrier), units and end-to-end rates summed."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device()) if torch.cuda.is_available() else torch.device("cpu")
+    v = torch.tensor([t_local, units_local, e2e_local], dtype=torch.float64, device=dev)
+    t = v[0:1].clone()
+    rest = v[1:].clone()
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(rest, op=dist.ReduceOp.SUM)
+    t_max, units, e2e = float(t.item()), float(rest[0].item()), float(rest[1].item())
+    return {"time_s": t_max, "units": units, "value": units / t_max, "e2e": e2e}
 
 
 def run_ours(args):
@@ -389,13 +431,6 @@ def run_ours(args):
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_local = float(np.sum(step_ms)) / 1e3
-    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
-    e = torch.tensor([float(np.sum(evals))], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(e, op=dist.ReduceOp.SUM)
-    t_max, e_tot = float(t.item()), float(e.item())
-    value = e_tot / t_max
 
     # end to end through the public API: host arrays in, results out
     res_bytes = 216 * len(problems)
@@ -408,10 +443,8 @@ def run_ours(args):
         out = sg.calibrate_batch(problems)
         e2e_t += time.perf_counter() - t0
         e2e_ev += sum(r.n_evals for r in out)
-    e2e_value_local = e2e_ev / e2e_t
-    ee = torch.tensor([e2e_value_local], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(ee, op=dist.ReduceOp.SUM)
+    agg = aggregate(t_local, float(np.sum(evals)), e2e_ev / e2e_t, dist)
+    t_max, value = agg["time_s"], agg["value"]
 
     # roofline of the dominant kernel: the SA level kernel (FP32 Hagan)
     lvl_ms = float(np.mean(level_ms))
@@ -419,15 +452,13 @@ def run_ours(args):
     achieved = quote_evals_per_launch / (lvl_ms / 1e3) / 1e9
     sm_mhz = clocks.get("sm_mhz") or 1920.0
     if rates:
-        sfu_rate = min(rates[1], rates[3], rates[4])   # ex2/rsqrt/rcp ops per SM clock
-        fp32_rate = rates[0]
-        peak_sfu = SMS * sfu_rate * sm_mhz * 1e6 / SFU_PER_QUOTE / 1e9
-        peak_fp32 = SMS * fp32_rate * sm_mhz * 1e6 / FP32_PER_QUOTE / 1e9
-        peak = min(peak_sfu, peak_fp32)
-        peak_note = "measured pipe rates (sabr_probe_pipe_rates) x 152 SMs x median SM clock"
+        peak_units, pipe, _ = pipe_bound(HAGAN_QUOTE_OPS, rates, sm_mhz)
+        peak = peak_units / 1e9
+        peak_note = ("measured pipe rates (sabr_probe_pipe_rates) x 152 SMs x median SM clock; binding pipe: %s"
+                     % pipe)
     else:
-        peak = SMS * 16 * sm_mhz * 1e6 / SFU_PER_QUOTE / 1e9
-        peak_note = "nominal 16 SFU ops/clk/SM x 152 SMs x median SM clock"
+        peak = SMS * sm_mhz * 1e6 / (1 / 32 + 4 / 16) / 1e9
+        peak_note = "nominal SFU rates (ex2 32, others 16 per SM clock) x 152 SMs x median SM clock"
     roofline = {"bound": "alu", "kernel": "sa_level_kernel<float,HAGAN>", "achieved": achieved, "peak": peak,
                 "unit": "Gquote-eval/s", "frac": achieved / peak, "traffic": None,
                 "launch_ms": lvl_ms, "quote_evals_per_launch": quote_evals_per_launch, "peak_from": peak_note,
@@ -441,7 +472,7 @@ def run_ours(args):
                                    "4096 SA chains/smile, 200 levels x 100 proposals, cooling 0.95",
                        "l2": "flushed (256 MB write) between timed steps", "precision": "FP32 bulk, FP64 sums"},
             "clocks": clocks, "gpu_launches": int(n_launch * args.steps),
-            "e2e": {"value": float(ee.item()), "unit": "cost-evals/s", "h2d_bytes_per_step": h2d,
+            "e2e": {"value": agg["e2e"], "unit": "cost-evals/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": res_bytes},
             "roofline": roofline}
 

@@ -60,18 +60,77 @@ template <class R> struct SmemQuotes {
   const R* mT;
 };
 
+// Double-float number hi + lo (|lo| <= ulp(hi)/2): sums of FP32 terms carried
+// to about 48 significant bits on the FP32 pipe.  GB300 issues FP64 at about
+// 1/75 of its FP32 rate, so the FP32 form keeps FP64 out of the per-proposal
+// path and sums the misfit in this format instead.
+struct DF {
+  float hi, lo;
+};
+// Exact sum a + b = s + e (Knuth's two-sum; no multiplies, so nothing is
+// contracted into an FMA).  Symmetric in a and b.
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  const float e = (a - (s - bb)) + (b - bb);
+  return DF{s, e};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const DF s = df_two_sum(a.hi, b.hi);
+  const float e = s.lo + (a.lo + b.lo);
+  const float hi = s.hi + e;
+  return DF{hi, e - (hi - s.hi)};
+}
+
+// Cost type of the working precision: double for FP64, DF for FP32.
+template <class R> struct CostOf {
+  using T = double;
+};
+template <> struct CostOf<float> {
+  using T = DF;
+};
+__device__ __forceinline__ double cost_from(double d, double) { return d; }
+__device__ __forceinline__ DF cost_from(double d, DF) {
+  const float hi = (float)d;
+  return DF{hi, (float)(d - (double)hi)};
+}
+__device__ __forceinline__ double cost_to_double(double c) { return c; }
+__device__ __forceinline__ double cost_to_double(DF c) { return (double)c.hi + (double)c.lo; }
+__device__ __forceinline__ bool cost_less(double a, double b) { return a < b; }
+__device__ __forceinline__ bool cost_less(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ bool cost_is_nan(double a) { return !(a == a); }
+__device__ __forceinline__ bool cost_is_nan(DF a) { return !(a.hi == a.hi); }
+__device__ __forceinline__ double cost_delta(double a, double b) { return a - b; }
+__device__ __forceinline__ float cost_delta(DF a, DF b) { return (a.hi - b.hi) + (a.lo - b.lo); }
+
 // ((market - model)/market)^2 term.  FP32 keeps 1/market (one FMA); FP64
 // divides exactly as written.
 __device__ __forceinline__ float resid(float v, float inv_mkt) { return 1.0f - v * inv_mkt; }
 __device__ __forceinline__ double resid(double v, double mkt) { return (mkt - v) / mkt; }
 
+// Sum over the G lanes of a chain by an xor butterfly: every lane ends with
+// the same, order-fixed total.  FP64 in the FP64 form; double-float in the
+// FP32 form.
+__device__ __forceinline__ double lanes_sum(double v, int G, unsigned gmask) {
+  for (int off = G >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(gmask, v, off);
+  return v;
+}
+__device__ __forceinline__ DF lanes_sum(float v, int G, unsigned gmask) {
+  DF s{v, 0.0f};
+  for (int off = G >> 1; off > 0; off >>= 1) {
+    const DF o{__shfl_xor_sync(gmask, s.hi, off), __shfl_xor_sync(gmask, s.lo, off)};
+    s = df_add(s, o);
+  }
+  return s;
+}
+
 // Cost of point xp evaluated by the G lanes of one chain group.  Lane `lane`
-// takes quotes lane, lane+G, ...; per-lane partial sums are combined by an
-// FP64 xor-butterfly (every lane ends with the same, order-fixed sum).
+// takes quotes lane, lane+G, ...; per-lane partial sums are combined by
+// lanes_sum.
 // For the dynamic models the lanes first compute the per-maturity polynomial
 // of eq. (vola_SABRd) into `coef` (this group's slice of shared memory).
 template <class R, int MODEL>
-__device__ __forceinline__ double group_cost(const R* xp, int n_quotes, int n_mats, R l2f,
+__device__ __forceinline__ typename CostOf<R>::T group_cost(const R* xp, int n_quotes, int n_mats, R l2f,
                                              const SmemQuotes<R>& sq, R* coef, int lane, int G,
                                              unsigned gmask) {
   R acc = (R)0;
@@ -113,9 +172,7 @@ __device__ __forceinline__ double group_cost(const R* xp, int n_quotes, int n_ma
     }
     __syncwarp(gmask);
   }
-  double s = (double)acc;
-  for (int off = G >> 1; off > 0; off >>= 1) s += __shfl_xor_sync(gmask, s, off);
-  return s;
+  return lanes_sum(acc, G, gmask);
 }
 
 }  // namespace sabr

@@ -49,6 +49,21 @@ __device__ __forceinline__ R warp_reduce_scatter32(R (&v)[32], int lane) {
   return v[0];
 }
 
+// Path state units: FP32 paths carry log2 F and log2 alpha, so that nu-hat =
+// alpha F^(beta-1) and F come from one SFU exp2 each; FP64 paths carry the
+// natural logarithms.  kLogUnit converts a natural-log increment.
+template <class R> struct PathUnits;
+template <> struct PathUnits<float> {
+  static constexpr double kLogUnit = 1.4426950408889634;  // 1/ln 2
+  __device__ static float expu(float x) { return exp2f(x); }
+  __host__ __device__ static double logu(double x) { return log2(x); }
+};
+template <> struct PathUnits<double> {
+  static constexpr double kLogUnit = 1.0;
+  __device__ static double expu(double x) { return exp(x); }
+  __host__ __device__ static double logu(double x) { return log(x); }
+};
+
 // Per-block step coefficients, in shared memory:
 //   a_i = nu_i sqrt(h_i)      (vol step)    b_i = -nu_i^2 h_i / 2
 //   c_i = rho_i sqrt(h_i)     d_i = sqrt(1 - rho_i^2) sqrt(h_i)
@@ -74,23 +89,29 @@ __device__ __forceinline__ void build_steps(const McDev& P, const double* p, Ste
       nu = p[3];
     }
     const double sh = sqrt(h);
+    const double u = PathUnits<R>::kLogUnit;
     StepCoef<R> s;
-    s.a = (R)(nu * sh);
-    s.b = (R)(-0.5 * nu * nu * h);
-    s.c = (R)(rho * sh);
-    s.d = (R)(sqrt(fmax(0.0, (1.0 - rho) * (1.0 + rho))) * sh);
-    s.e = (R)(-0.5 * h);
+    s.a = (R)(u * nu * sh);
+    s.b = (R)(-0.5 * u * nu * nu * h);
+    s.c = (R)(u * rho * sh);
+    s.d = (R)(u * sqrt(fmax(0.0, (1.0 - rho) * (1.0 + rho))) * sh);
+    s.e = (R)(-0.5 * u * h);
     tab[i] = s;
     smat[i] = P.step_mat[i];
   }
 }
 
+// FP32: SFU forms.  -2 ln u1 lies in (0, 34] for u1 in [2^-24, 1 - 2^-24], so
+// sqrt = s rsqrt(s); the angle 2 pi u2 - pi lies in (-pi, pi), where the SFU
+// sine and cosine keep an absolute error below 2^-21, and
+// (cos, sin)(2 pi u2) = -(cos, sin)(2 pi u2 - pi).
 __device__ __forceinline__ void box_muller(float u1, float u2, float& z1, float& z2) {
-  const float r = sqrtf(-2.0f * logf(u1));
+  const float s2 = -2.0f * __logf(u1);
+  const float r = s2 * rsqrtf(s2);
   float s, c;
-  sincospif(2.0f * u2, &s, &c);
-  z1 = r * c;
-  z2 = r * s;
+  __sincosf(6.28318530717958647692f * u2 - 3.14159265358979323846f, &s, &c);
+  z1 = -r * c;
+  z2 = -r * s;
 }
 __device__ __forceinline__ void box_muller(double u1, double u2, double& z1, double& z2) {
   const double r = sqrt(-2.0 * log(u1));
@@ -113,8 +134,8 @@ __device__ __forceinline__ void simulate_paths(const McDev& P, const double* p,
                                                int64_t pstride, double* wacc) {
   const int lane = threadIdx.x & 31;
   const R beta_m1 = (R)(p[1] - 1.0);
-  const R lnf = (R)log(P.fwd), lna = (R)log(p[0]);
-  const R log_abs = (R)P.log_absorb;
+  const R lnf = (R)PathUnits<R>::logu(P.fwd), lna = (R)PathUnits<R>::logu(p[0]);
+  const R log_abs = (R)(P.log_absorb * PathUnits<R>::kLogUnit);
   const int64_t n_paths = P.n_paths;
   // every lane of the warp runs the same trip count (idle lanes pay 0)
   const int64_t warp_path0 = path0 - lane;
@@ -131,13 +152,13 @@ __device__ __forceinline__ void simulate_paths(const McDev& P, const double* p,
       R z1, z2;
       box_muller(u01<R>(wa), u01<R>(wb), z1, z2);
       const StepCoef<R> s = tab[i];
-      const R nuhat = m_exp(lnA + beta_m1 * lnF);  // old alpha, old F
+      const R nuhat = PathUnits<R>::expu(lnA + beta_m1 * lnF);  // old alpha, old F
       lnF = lnF + nuhat * (s.c * z1 + s.d * z2) + nuhat * nuhat * s.e;
       lnA = lnA + s.a * z1 + s.b;
       absorbed = absorbed || !(lnF >= log_abs);
       const int m = smat[i];
       if (m >= 0) {
-        const R F = absorbed || !live ? (R)0 : m_exp(lnF);
+        const R F = absorbed || !live ? (R)0 : PathUnits<R>::expu(lnF);
         const int q0 = s_q0[m], nq = s_nq[m], slot0 = s_slot[m];
         for (int c0 = 0; c0 < 2 * nq; c0 += 32) {
           R v[32];

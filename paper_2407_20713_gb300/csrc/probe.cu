@@ -27,7 +27,8 @@ __device__ __forceinline__ float probe_op_f(float x, float a, float b) {
   } else if (OP == 3) {
     asm volatile("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   } else if (OP == 4) {
-    asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    // x -> 1/(x + 1): a chain of reciprocals that cannot fold into identity
+    asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x + 1.0f));
   } else {
     asm volatile("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   }

@@ -77,10 +77,12 @@ __device__ __forceinline__ float propose(float x, float step, float u) {
 __device__ __forceinline__ double propose(double x, double step, double u) {
   return __dadd_rn(x, __dmul_rn(step, __dsub_rn(__dmul_rn(2.0, u), 1.0)));
 }
-__device__ __forceinline__ bool metropolis(float u, double delta, double Tk) {
-  return u < __expf((float)(-delta / Tk));
+// Metropolis acceptance of an uphill move (delta > 0) at temperature Tk.
+// FP32 form: FP32 arithmetic with 1/Tk formed once per level.
+__device__ __forceinline__ bool metropolis(float u, float delta, float inv_Tk, double) {
+  return u < __expf(-delta * inv_Tk);
 }
-__device__ __forceinline__ bool metropolis(double u, double delta, double Tk) {
+__device__ __forceinline__ bool metropolis(double u, double delta, float, double Tk) {
   return u < exp(-delta / Tk);
 }
 
@@ -101,7 +103,8 @@ __global__ void sa_init_kernel(const ProblemDev* __restrict__ probs, const int* 
 #pragma unroll
   for (int i = 0; i < kMaxD; ++i) x[i] = (R)P.x0[i];
   double f0 = 0.0;
-  if (lane < G) f0 = group_cost<R, MODEL>(x, P.n_quotes, P.n_mats, (R)P.l2f, sq, coef, lane, G, group_mask(G));
+  if (lane < G)
+    f0 = cost_to_double(group_cost<R, MODEL>(x, P.n_quotes, P.n_mats, (R)P.l2f, sq, coef, lane, G, group_mask(G)));
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int i = 0; i < kMaxD; ++i) P.state[i] = (double)x[i];
@@ -149,15 +152,17 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
     lo[i] = (R)P.lo[i];
     hi[i] = (R)P.hi[i];
   }
-  double fcur = P.state[kMaxD];
-  double bf = fcur;
+  using C = typename CostOf<R>::T;
+  C fcur = cost_from(P.state[kMaxD], C{});
+  C bf = fcur;
+  const float inv_Tk = (float)(1.0 / Tk);
   R* cbx = (R*)P.chain_bx + (size_t)chain * kMaxD;
   if (active) {
     if (level == 0) {
 #pragma unroll
       for (int i = 0; i < D; ++i) bx[i] = x[i];
     } else {
-      bf = P.chain_bf[chain];
+      bf = cost_from(P.chain_bf[chain], C{});
 #pragma unroll
       for (int i = 0; i < D; ++i) bx[i] = cbx[i];
     }
@@ -170,17 +175,32 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
     for (int st = 0; st < P.chain_len; ++st) {
       // D move uniforms and one acceptance uniform: words 0..D of Philox
       // blocks 0, 1, ... with counter (chain, level, step, tag + block).
+      // With G >= NB lanes, lane b computes block b once for the chain and
+      // the words are gathered by shuffles; otherwise each lane computes all.
       constexpr int NB = (D + 4) / 4;
       R u[4 * NB];
-#pragma unroll
-      for (int b = 0; b < NB; ++b) {
+      if (G >= NB) {
+        const int b = lane < NB ? lane : 0;
         const uint4 w = philox4x32_10(
             make_uint4((uint32_t)chain, (uint32_t)level, (uint32_t)st, kTagSA + (uint32_t)b), P.key0,
             P.key1);
-        u[4 * b + 0] = u01<R>(w.x);
-        u[4 * b + 1] = u01<R>(w.y);
-        u[4 * b + 2] = u01<R>(w.z);
-        u[4 * b + 3] = u01<R>(w.w);
+        const int base = (threadIdx.x & 31) & ~(G - 1);
+#pragma unroll
+        for (int i = 0; i <= D; ++i) {
+          const uint32_t word = (i & 3) == 0 ? w.x : ((i & 3) == 1 ? w.y : ((i & 3) == 2 ? w.z : w.w));
+          u[i] = u01<R>(__shfl_sync(gmask, word, base + (i >> 2)));
+        }
+      } else {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          const uint4 w = philox4x32_10(
+              make_uint4((uint32_t)chain, (uint32_t)level, (uint32_t)st, kTagSA + (uint32_t)b), P.key0,
+              P.key1);
+          u[4 * b + 0] = u01<R>(w.x);
+          u[4 * b + 1] = u01<R>(w.y);
+          u[4 * b + 2] = u01<R>(w.z);
+          u[4 * b + 3] = u01<R>(w.w);
+        }
       }
       R xp[D];
       bool inside = true;
@@ -191,16 +211,16 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
       }
       if (MODEL == SABR_DYN_II && inside) inside = case2_feasible<R>(xp, Tmax);
       if (!inside) continue;
-      const double fp = group_cost<R, MODEL>(xp, P.n_quotes, P.n_mats, l2f, sq, coef, lane, G, gmask);
+      const C fp = group_cost<R, MODEL>(xp, P.n_quotes, P.n_mats, l2f, sq, coef, lane, G, gmask);
       ++ev;
-      if (!(fp == fp)) continue;
-      if (fp < bf) {
+      if (cost_is_nan(fp)) continue;
+      if (cost_less(fp, bf)) {
         bf = fp;
 #pragma unroll
         for (int i = 0; i < D; ++i) bx[i] = xp[i];
       }
-      const double delta = fp - fcur;
-      if (delta <= 0.0 || metropolis(u[D], delta, Tk)) {
+      const auto delta = cost_delta(fp, fcur);
+      if (delta <= 0 || metropolis(u[D], delta, inv_Tk, Tk)) {
 #pragma unroll
         for (int i = 0; i < D; ++i) x[i] = xp[i];
         fcur = fp;
@@ -208,7 +228,7 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
       }
     }
     if (lane == 0) {
-      P.chain_bf[chain] = bf;
+      P.chain_bf[chain] = cost_to_double(bf);
 #pragma unroll
       for (int i = 0; i < kMaxD; ++i) cbx[i] = i < D ? bx[i] : (R)0;
       if (level == 0) {
@@ -218,7 +238,7 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
         P.chain_ev[chain] += ev;
         P.chain_ac[chain] += ac;
       }
-      red_f[g] = fcur;
+      red_f[g] = cost_to_double(fcur);
 #pragma unroll
       for (int i = 0; i < kMaxD; ++i) red_x[g * kMaxD + i] = i < D ? x[i] : (R)0;
     }
@@ -261,7 +281,7 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
 }
 
 template <class R, int MODEL>
-__global__ void __launch_bounds__(kSaBlock) sa_level_kernel(const ProblemDev* __restrict__ probs,
+__global__ void __launch_bounds__(kSaBlock, sizeof(R) == 4 ? 3 : 1) sa_level_kernel(const ProblemDev* __restrict__ probs,
                                                            const int2* __restrict__ bmap, int level) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ ProblemDev P;
@@ -275,7 +295,7 @@ __global__ void __launch_bounds__(kSaBlock) sa_level_kernel(const ProblemDev* __
 // w < *n_work, read from device memory so one captured launch serves every
 // step whatever its mix of requests.
 template <class R, int MODEL>
-__global__ void __launch_bounds__(kSaBlock) sa_level_persistent(const ProblemDev* __restrict__ probs,
+__global__ void __launch_bounds__(kSaBlock, sizeof(R) == 4 ? 3 : 1) sa_level_persistent(const ProblemDev* __restrict__ probs,
                                                                const int4* __restrict__ work,
                                                                const int* __restrict__ n_work) {
   extern __shared__ __align__(16) unsigned char smem[];

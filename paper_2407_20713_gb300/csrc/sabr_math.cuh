@@ -40,6 +40,12 @@ __device__ __forceinline__ float m_expm1(float x) { return expm1f(x); }
 __device__ __forceinline__ double m_expm1(double x) { return expm1(x); }
 __device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
+// Hot-loop division and square root: in FP32 the SFU reciprocal / rsqrt
+// forms (about 2 ulp), in FP64 the IEEE operations.
+__device__ __forceinline__ float m_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double m_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float m_sqrt_pos(float x) { return x * rsqrtf(x); }  // x > 0
+__device__ __forceinline__ double m_sqrt_pos(double x) { return sqrt(x); }
 
 // ---------------------------------------------------------------------------
 // Compile-time tables: factorials and Gauss-Legendre rules (nodes found by
@@ -127,18 +133,34 @@ template <class R> __device__ __forceinline__ R u01(uint32_t w) {
 // opr = 1 + rho are passed in, formed from the FP64 parameter.
 // ---------------------------------------------------------------------------
 template <class R>
-__device__ __forceinline__ R z_over_x(R z, R rho, R omr, R opr) {
-  if (z == (R)0) return (R)1;
+__device__ __forceinline__ R x_of_z(R z, R rho, R omr, R opr) {
   const R zr = z - rho;
-  const R D = m_sqrt(zr * zr + omr * opr);
-  R x;
+  const R D = m_sqrt_pos(zr * zr + omr * opr);
   if (z < (R)1) {
-    const R w = (R)2 * z / ((R)1 - z + D);
-    x = (w >= (R)-0.5) ? m_log1p(w) : m_log(opr / (D - zr));
-  } else {
-    x = m_log((D + zr) / omr);
+    const R w = m_div((R)2 * z, (R)1 - z + D);
+    return (w >= (R)-0.5) ? m_log1p(w) : m_log(m_div(opr, D - zr));
   }
-  return z / x;
+  return m_log(m_div(D + zr, omr));
+}
+
+// z/x(z) as a quotient zn/xd (1/1 at z = 0), so callers fold it into their
+// own single division.
+template <class R>
+__device__ __forceinline__ void z_over_x_parts(R z, R rho, R omr, R opr, R& zn, R& xd) {
+  if (z == (R)0) {
+    zn = (R)1;
+    xd = (R)1;
+  } else {
+    zn = z;
+    xd = x_of_z<R>(z, rho, omr, opr);
+  }
+}
+
+template <class R>
+__device__ __forceinline__ R z_over_x(R z, R rho, R omr, R opr) {
+  R zn, xd;
+  z_over_x_parts<R>(z, rho, omr, opr, zn, xd);
+  return m_div(zn, xd);
 }
 
 // ---------------------------------------------------------------------------
@@ -179,9 +201,10 @@ __device__ __forceinline__ R vol_hagan(const StaticConst<R>& s, R lfk, R l2kf, R
   const R L2 = lfk * lfk;
   const R den = (R)1 + L2 * (s.c2 + s.c4 * L2);
   const R z = s.nu_over_alpha * fk * lfk;
-  const R zx = z_over_x<R>(z, s.rho, s.omr, s.opr);
+  R zn, xd;
+  z_over_x_parts<R>(z, s.rho, s.omr, s.opr, zn, xd);
   const R brk = (R)1 + (s.br_a * fkinv * fkinv + s.br_b * fkinv + s.br_c) * T;
-  return s.alpha * fkinv * zx * brk / den;
+  return m_div(s.alpha * fkinv * zn * brk, den * xd);
 }
 
 // eq. (sigma-SABR): z = nu (f^{1-b} - K^{1-b}) / (alpha (1-b)); the
@@ -190,14 +213,18 @@ __device__ __forceinline__ R vol_hagan(const StaticConst<R>& s, R lfk, R l2kf, R
 template <class R>
 __device__ __forceinline__ R vol_obloj(const StaticConst<R>& s, R lfk, R l2kf, R l2k, R T) {
   const R kpow = m_exp2(s.omb * l2k);  // K^{1-beta}
-  const R zd = (s.omb == (R)0) ? lfk : kpow * m_expm1(s.omb * lfk) / s.omb;
-  const R z = s.nu * zd / s.alpha;
-  const R lead = (lfk == (R)0) ? s.alpha / kpow : s.alpha * lfk / zd;
+  const R zd = (s.omb == (R)0) ? lfk : m_div(kpow * m_expm1(s.omb * lfk), s.omb);
+  const R z = s.nu_over_alpha * zd;
+  // lead = alpha lfk / zd, or alpha / K^{1-beta} at the money
+  const R ln = (lfk == (R)0) ? s.alpha : s.alpha * lfk;
+  const R ld = (lfk == (R)0) ? kpow : zd;
   const R fkinv = m_exp2(-s.half_omb * l2kf);
   const R L2 = lfk * lfk;
   const R den = (R)1 + L2 * (s.c2 + s.c4 * L2);
   const R brk = (R)1 + (s.br_a * fkinv * fkinv + s.br_b * fkinv + s.br_c) * T;
-  return lead * z_over_x<R>(z, s.rho, s.omr, s.opr) * brk / den;
+  R zn, xd;
+  z_over_x_parts<R>(z, s.rho, s.omr, s.opr, zn, xd);
+  return m_div(ln * zn * brk, ld * xd * den);
 }
 
 // ---------------------------------------------------------------------------
