@@ -77,6 +77,9 @@ def lib():
         L.orc_mc_price.argtypes = [ctypes.c_int, _PD, _D, _PD, _PD, _PI8, _PD, _I64,
                                    _I64, _D, ctypes.c_uint64, ctypes.c_int, _PD, _PD]
         L.orc_mc_price.restype = ctypes.c_int
+        L.orc_mc_cliquet.argtypes = [ctypes.c_int, _PD, _D, _D, ctypes.c_int, _D, _D, _D, _D, _D, _I64, _D,
+                                     ctypes.c_uint64, ctypes.c_int, _PD, _PD]
+        L.orc_mc_cliquet.restype = ctypes.c_int
         L.orc_sa_calibrate.argtypes = [
             ctypes.c_int, ctypes.c_int, _D, _I64, _PD, _PD, _PD, _PD, _PI8,
             ctypes.c_int, _I64, _D, ctypes.c_uint64, _PD, _PD, _PD,
@@ -255,3 +258,16 @@ def sa_calibrate(model, f, T, K, mkt, lo, hi, *, cost=COST_VOL, n_chains=64,
     if trace:
         out["trace"] = tr[:n_levels].copy()
     return out
+
+
+def mc_cliquet(model, p, f, T, n_resets, floor_l, cap_l, floor_g, cap_g, disc=1.0, n_paths=1 << 12,
+               steps_per_year=250.0, seed=0, n_threads=1):
+    """Sec. 6.3 cliquet price and standard error."""
+    q = _params(p)
+    price, se = ctypes.c_double(), ctypes.c_double()
+    rc = lib().orc_mc_cliquet(model, _dp(q), float(f), float(T), int(n_resets), float(floor_l), float(cap_l),
+                              float(floor_g), float(cap_g), float(disc), int(n_paths), float(steps_per_year),
+                              int(seed) & 0xFFFFFFFFFFFFFFFF, int(n_threads), ctypes.byref(price), ctypes.byref(se))
+    if rc != 0:
+        raise ValueError("orc_mc_cliquet rejected its input")
+    return price.value, se.value

@@ -453,52 +453,73 @@ int64_t orc_mc_grid(const double* T, int64_t n, double spy, double* grid,
   return cnt;
 }
 
-/* Path j of the log-Euler scheme, eq. (dis_SABRd), with left-point nu(t_i),
- * rho(t_i) and the OLD alpha_i in nu-hat.  Absorption (a reading; the paper
- * is silent): once F < 1e-12 f the path is frozen at F = 0.  At each grid
- * point that is a maturity the payoffs of the options of that maturity are
- * added to sum[] and sumsq[]. */
+/* State of one path of the log-Euler scheme. */
+typedef struct {
+  double F, alpha, t;
+  int absorbed;
+  uint32_t w[4];
+} mc_state;
+
+static void mc_start(const double* p, double f, mc_state* s) {
+  s->F = f;
+  s->alpha = p[0];
+  s->t = 0.0;
+  s->absorbed = 0;
+  s->w[0] = s->w[1] = s->w[2] = s->w[3] = 0;
+}
+
+/* Step i of path `path` (from s->t to grid[i]) of the log-Euler scheme,
+ * eq. (dis_SABRd), with left-point nu(t_i), rho(t_i) and the OLD alpha_i in
+ * nu-hat.  The normals of steps 2m and 2m+1 come from Philox block
+ * (path, m, 0, tag) by Box-Muller.  Absorption (a reading; the paper is
+ * silent): once F < 1e-12 f the path is frozen at F = 0. */
+static void mc_step(int model, const double* p, double absorb_at, const double* grid, int64_t i,
+                    uint32_t path, const uint32_t key[2], mc_state* s) {
+  int dyn = (model == ORC_DYN_I) ? 1 : (model == ORC_DYN_II ? 2 : 0);
+  double beta = p[1];
+  double h = grid[i] - s->t;
+  if ((i & 1) == 0) {
+    uint32_t ctr[4] = {path, (uint32_t)(i >> 1), 0u, ORC_TAG_MC};
+    orc_philox4x32_10(ctr, key, s->w);
+  }
+  uint32_t wa = (i & 1) ? s->w[2] : s->w[0], wb = (i & 1) ? s->w[3] : s->w[1];
+  double z1, z2;
+  orc_box_muller(orc_u01(wa), orc_u01(wb), &z1, &z2);
+  double nu = dyn ? orc_nu_t(dyn, p, s->t) : p[3];
+  double rho = dyn ? orc_rho_t(dyn, p, s->t) : p[2];
+  double sh = sqrt(h);
+  if (!s->absorbed) {
+    double nuhat = s->alpha * pow(s->F, beta - 1.0);
+    double Fn = s->F * exp(nuhat * (rho * z1 + sqrt(1.0 - rho * rho) * z2) * sh -
+                           nuhat * nuhat * h / 2.0);
+    if (!(Fn >= absorb_at)) {
+      s->absorbed = 1;
+      s->F = 0.0;
+    } else {
+      s->F = Fn;
+    }
+  }
+  s->alpha = s->alpha * exp(nu * z1 * sh - nu * nu * h / 2.0);
+  s->t = grid[i];
+}
+
+/* Path j of the scheme; at each grid point that is a maturity the payoffs
+ * of the options of that maturity are added to sum[] and sumsq[]. */
 static void mc_path(int model, const double* p, double f, const double* grid,
                     int64_t n_steps, const double* T, const double* K,
                     const int8_t* is_call, const int64_t* qorder, int64_t n,
                     uint32_t path, const uint32_t key[2], double* sum,
                     double* sumsq) {
-  int dyn = (model == ORC_DYN_I) ? 1 : (model == ORC_DYN_II ? 2 : 0);
-  double alpha = p[0], beta = p[1];
-  double F = f, absorb_at = 1e-12 * f;
-  int absorbed = 0;
-  double t = 0.0;
+  mc_state st;
+  mc_start(p, f, &st);
   int64_t qi = 0;
-  uint32_t w[4] = {0, 0, 0, 0};
   for (int64_t i = 0; i < n_steps; ++i) {
-    double h = grid[i] - t;
-    if ((i & 1) == 0) {
-      uint32_t ctr[4] = {path, (uint32_t)(i >> 1), 0u, ORC_TAG_MC};
-      orc_philox4x32_10(ctr, key, w);
-    }
-    uint32_t wa = (i & 1) ? w[2] : w[0], wb = (i & 1) ? w[3] : w[1];
-    double z1, z2;
-    orc_box_muller(orc_u01(wa), orc_u01(wb), &z1, &z2);
-    double nu = dyn ? orc_nu_t(dyn, p, t) : p[3];
-    double rho = dyn ? orc_rho_t(dyn, p, t) : p[2];
-    double sh = sqrt(h);
-    if (!absorbed) {
-      double nuhat = alpha * pow(F, beta - 1.0);
-      double Fn = F * exp(nuhat * (rho * z1 + sqrt(1.0 - rho * rho) * z2) * sh -
-                          nuhat * nuhat * h / 2.0);
-      if (!(Fn >= absorb_at)) {
-        absorbed = 1;
-        F = 0.0;
-      } else {
-        F = Fn;
-      }
-    }
-    alpha = alpha * exp(nu * z1 * sh - nu * nu * h / 2.0);
-    t = grid[i];
+    mc_step(model, p, 1e-12 * f, grid, i, path, key, &st);
     /* quotes sorted by maturity: pay those that mature at this grid point */
-    while (qi < n && fabs(T[qorder[qi]] - t) <= 1e-10) {
+    while (qi < n && fabs(T[qorder[qi]] - st.t) <= 1e-10) {
       int64_t q = qorder[qi++];
       int call = is_call ? is_call[q] != 0 : 1;
+      double F = st.F;
       double pay = call ? (F > K[q] ? F - K[q] : 0.0) : (K[q] > F ? K[q] - F : 0.0);
       sum[q] += pay;
       sumsq[q] += pay * pay;
@@ -560,6 +581,78 @@ int orc_mc_price(int model, const double* p, double f, const double* T,
   free(part);
   free(grid);
   free(qorder);
+  return 0;
+}
+
+/* Cliquet of Sec. 6.3 on one path: F is recorded at the reset dates
+ * d_1 < ... < d_n (grid points), R_i = F(d_i)/F(d_{i-1}) - 1 for i = 2..n,
+ * eq. (eq_cliquet) sums max(min(R_i, cap_l), floor_l), and the global limits
+ * give max(floor_g, min(cap_g, sum)) (eq. (cliquet_global) with its two
+ * limits in the order that makes floor_g a floor).  A path absorbed before
+ * d_{i-1} has F(d_{i-1}) = 0 and contributes R_i = 0 (0 to 0); absorbed
+ * between d_{i-1} and d_i it contributes R_i = -1. */
+static double cliquet_path(int model, const double* p, double f, const double* grid,
+                           int64_t n_steps, const double* resets, int n_resets,
+                           double floor_l, double cap_l, double floor_g, double cap_g,
+                           uint32_t path, const uint32_t key[2]) {
+  mc_state st;
+  mc_start(p, f, &st);
+  int ri = 0;
+  double prev = 0.0, sum = 0.0;
+  for (int64_t i = 0; i < n_steps; ++i) {
+    mc_step(model, p, 1e-12 * f, grid, i, path, key, &st);
+    if (ri < n_resets && fabs(resets[ri] - st.t) <= 1e-10) {
+      if (ri >= 1) {
+        double R = prev > 0.0 ? st.F / prev - 1.0 : 0.0;
+        double c = R < cap_l ? R : cap_l;
+        sum += c > floor_l ? c : floor_l;
+      }
+      prev = st.F;
+      ++ri;
+    }
+  }
+  double g = sum < cap_g ? sum : cap_g;
+  return g > floor_g ? g : floor_g;
+}
+
+int orc_mc_cliquet(int model, const double* p, double f, double T, int n_resets,
+                   double floor_l, double cap_l, double floor_g, double cap_g,
+                   double disc, int64_t n_paths, double spy, uint64_t seed,
+                   int n_threads, double* price, double* se) {
+  if (!(T > 0.0) || n_resets < 2 || n_paths <= 1 || !(spy > 0.0) || !(f > 0.0)) return -1;
+  if (!orc_feasible(model, p, T)) return -1;
+  double* resets = (double*)malloc(sizeof(double) * n_resets);
+  for (int i = 0; i < n_resets; ++i) resets[i] = (double)(i + 1) * T / n_resets;
+  int64_t n_steps = orc_mc_grid(resets, n_resets, spy, NULL, 0);
+  double* grid = (double*)malloc(sizeof(double) * n_steps);
+  orc_mc_grid(resets, n_resets, spy, grid, n_steps);
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  const int64_t BLK = 4096;
+  int64_t nblk = (n_paths + BLK - 1) / BLK;
+  double* part = (double*)calloc((size_t)nblk * 2, sizeof(double));
+  if (n_threads < 1) n_threads = 1;
+#pragma omp parallel for schedule(dynamic) num_threads(n_threads)
+  for (int64_t b = 0; b < nblk; ++b) {
+    int64_t j1 = (b + 1) * BLK < n_paths ? (b + 1) * BLK : n_paths;
+    for (int64_t j = b * BLK; j < j1; ++j) {
+      double v = cliquet_path(model, p, f, grid, n_steps, resets, n_resets, floor_l, cap_l,
+                              floor_g, cap_g, (uint32_t)j, key);
+      part[2 * b] += v;
+      part[2 * b + 1] += v * v;
+    }
+  }
+  double s = 0.0, s2 = 0.0;
+  for (int64_t b = 0; b < nblk; ++b) {
+    s += part[2 * b];
+    s2 += part[2 * b + 1];
+  }
+  double N = (double)n_paths, mean = s / N, var = (s2 - s * mean) / (N - 1.0);
+  if (var < 0.0) var = 0.0;
+  *price = disc * mean;
+  if (se) *se = disc * sqrt(var / N);
+  free(part);
+  free(grid);
+  free(resets);
   return 0;
 }
 

@@ -109,6 +109,17 @@ int orc_mc_price(int model, const double* p, double f, const double* T,
                  int64_t n, int64_t n_paths, double steps_per_year,
                  uint64_t seed, int n_threads, double* price, double* stderr_out);
 
+/* Sec. 6.3, eqs. (eq_cliquet), (cliquet_global): a cliquet on the forward
+ * with reset dates d_i = i T / n_resets (i = 1 .. n_resets), paying
+ * sum_{i=2..n} max(min(R_i, cap_l), floor_l), R_i = F(d_i)/F(d_{i-1}) - 1,
+ * then max(floor_g, min(cap_g, .)) (the printed global formula has the two
+ * limits swapped; with floor_g = 0 < cap_g it would be constant), times
+ * disc.  Same paths as orc_mc_price (grid with the reset dates inserted). */
+int orc_mc_cliquet(int model, const double* p, double f, double T, int n_resets,
+                   double floor_l, double cap_l, double floor_g, double cap_g,
+                   double disc, int64_t n_paths, double steps_per_year,
+                   uint64_t seed, int n_threads, double* price, double* se);
+
 /* The step grid the MC walks: multiples of 1/steps_per_year with every
  * maturity inserted.  Writes up to cap points; returns the count. */
 int64_t orc_mc_grid(const double* T, int64_t n, double steps_per_year,
