@@ -144,14 +144,19 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
   double sk = __dmul_rn(P.step0, __dsqrt_rn(__ddiv_rn(Tk, T0)));
   if (sk < P.step_min) sk = P.step_min;
 
-  R x[D], bx[D], step[D], lo[D], hi[D];
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-    x[i] = (R)P.state[i];
-    step[i] = (R)__dmul_rn(sk, __dsub_rn(P.hi[i], P.lo[i]));
-    lo[i] = (R)P.lo[i];
-    hi[i] = (R)P.hi[i];
+  // box and step widths of this level, shared by the block's chains (kept
+  // in shared memory rather than registers)
+  __shared__ R s_lo[kMaxD], s_hi[kMaxD], s_step[kMaxD];
+  if (threadIdx.x < D) {
+    const int i = threadIdx.x;
+    s_step[i] = (R)__dmul_rn(sk, __dsub_rn(P.hi[i], P.lo[i]));
+    s_lo[i] = (R)P.lo[i];
+    s_hi[i] = (R)P.hi[i];
   }
+  __syncthreads();
+  R x[D], bx[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) x[i] = (R)P.state[i];
   using C = typename CostOf<R>::T;
   C fcur = cost_from(P.state[kMaxD], C{});
   C bf = fcur;
@@ -167,27 +172,37 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
       for (int i = 0; i < D; ++i) bx[i] = cbx[i];
     }
   }
-  unsigned long long ev = 0, ac = 0;
+  unsigned ev = 0, ac = 0;  // per level: at most chain_len each
   const R l2f = (R)P.l2f;
   const R Tmax = (R)P.Tmax;
 
   if (active) {
+    uint4 wbuf = make_uint4(0u, 0u, 0u, 0u);
+    constexpr int NB = (D + 4) / 4;       // Philox blocks per step
+    const int S = G >= NB ? G / NB : 1;  // steps per batch of Philox blocks
+    int s_ctr = 0;                         // st mod S
     for (int st = 0; st < P.chain_len; ++st) {
       // D move uniforms and one acceptance uniform: words 0..D of Philox
       // blocks 0, 1, ... with counter (chain, level, step, tag + block).
-      // With G >= NB lanes, lane b computes block b once for the chain and
-      // the words are gathered by shuffles; otherwise each lane computes all.
-      constexpr int NB = (D + 4) / 4;
+      // With G >= NB lanes, the chain's lanes compute the blocks of S = G/NB
+      // consecutive steps at once (lane l: step st0 + l/NB, block l%NB) and
+      // every step gathers its words by shuffles; otherwise each lane
+      // computes all NB blocks of every step.
       R u[4 * NB];
       if (G >= NB) {
-        const int b = lane < NB ? lane : 0;
-        const uint4 w = philox4x32_10(
-            make_uint4((uint32_t)chain, (uint32_t)level, (uint32_t)st, kTagSA + (uint32_t)b), P.key0,
-            P.key1);
-        const int base = (threadIdx.x & 31) & ~(G - 1);
+        const int s_in = s_ctr;
+        s_ctr = s_ctr + 1 == S ? 0 : s_ctr + 1;
+        if (s_in == 0) {
+          const int l = lane < S * NB ? lane : 0;
+          wbuf = philox4x32_10(make_uint4((uint32_t)chain, (uint32_t)level, (uint32_t)(st + l / NB),
+                                          kTagSA + (uint32_t)(l % NB)),
+                               P.key0, P.key1);
+        }
+        const int base = ((threadIdx.x & 31) & ~(G - 1)) + s_in * NB;
 #pragma unroll
         for (int i = 0; i <= D; ++i) {
-          const uint32_t word = (i & 3) == 0 ? w.x : ((i & 3) == 1 ? w.y : ((i & 3) == 2 ? w.z : w.w));
+          const uint32_t word =
+              (i & 3) == 0 ? wbuf.x : ((i & 3) == 1 ? wbuf.y : ((i & 3) == 2 ? wbuf.z : wbuf.w));
           u[i] = u01<R>(__shfl_sync(gmask, word, base + (i >> 2)));
         }
       } else {
@@ -206,8 +221,8 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
       bool inside = true;
 #pragma unroll
       for (int i = 0; i < D; ++i) {
-        xp[i] = propose(x[i], step[i], u[i]);
-        inside = inside && !(xp[i] < lo[i] || xp[i] > hi[i]);
+        xp[i] = propose(x[i], s_step[i], u[i]);
+        inside = inside && !(xp[i] < s_lo[i] || xp[i] > s_hi[i]);
       }
       if (MODEL == SABR_DYN_II && inside) inside = case2_feasible<R>(xp, Tmax);
       if (!inside) continue;

@@ -45,6 +45,10 @@ __device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float m_div(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double m_div(double a, double b) { return a / b; }
 __device__ __forceinline__ float m_sqrt_pos(float x) { return x * rsqrtf(x); }  // x > 0
+// Division by a constant: FP32 multiplies by the rounded reciprocal (one
+// extra rounding), FP64 divides as written.
+__device__ __forceinline__ float m_divc(float a, double c) { return a * (float)(1.0 / c); }
+__device__ __forceinline__ double m_divc(double a, double c) { return a / c; }
 __device__ __forceinline__ double m_sqrt_pos(double x) { return sqrt(x); }
 
 // ---------------------------------------------------------------------------
@@ -182,12 +186,12 @@ __device__ __forceinline__ StaticConst<R> static_setup(const P* x) {
   s.nu = (R)x[3];
   s.omb = (R)1 - s.beta;
   s.half_omb = (R)0.5 * s.omb;
-  s.c2 = s.omb * s.omb / (R)24;
-  s.c4 = s.omb * s.omb * s.omb * s.omb / (R)1920;
-  s.nu_over_alpha = s.nu / s.alpha;
+  s.c2 = m_divc(s.omb * s.omb, 24.0);
+  s.c4 = m_divc(s.omb * s.omb * s.omb * s.omb, 1920.0);
+  s.nu_over_alpha = m_div(s.nu, s.alpha);
   s.br_a = s.c2 * s.alpha * s.alpha;
   s.br_b = (R)0.25 * s.rho * s.beta * s.nu * s.alpha;
-  s.br_c = ((R)2 - (R)3 * s.rho * s.rho) / (R)24 * s.nu * s.nu;
+  s.br_c = m_divc((R)2 - (R)3 * s.rho * s.rho, 24.0) * s.nu * s.nu;
   s.omr = (R)1 - s.rho;
   s.opr = (R)1 + s.rho;
   return s;
@@ -240,16 +244,16 @@ template <class R, class P>
 __device__ __forceinline__ PolyCoef<R> expanded_coef(const P* x, R l2f, R T) {
   const R alpha = (R)x[0], beta = (R)x[1], rho = (R)x[2], nu = (R)x[3];
   const R omb = (R)1 - beta;
-  const R w = m_exp2(omb * l2f) / alpha;
+  const R w = m_div(m_exp2(omb * l2f), alpha);
   const R rnw = rho * nu * w;
   const R A1 = (R)-0.5 * (omb - rnw);
-  const R A2 = (omb * omb + (R)3 * (omb - rnw) + ((R)2 - (R)3 * rho * rho) * nu * nu * w * w) / (R)12;
-  const R B = omb * omb / ((R)24 * w * w) + beta * rho * nu / ((R)4 * w) +
-              ((R)2 - (R)3 * rho * rho) / (R)24 * nu * nu;
+  const R A2 = m_divc(omb * omb + (R)3 * (omb - rnw) + ((R)2 - (R)3 * rho * rho) * nu * nu * w * w, 12.0);
+  const R B = m_div(omb * omb, (R)24 * w * w) + m_div(beta * rho * nu, (R)4 * w) +
+              m_divc((R)2 - (R)3 * rho * rho, 24.0) * nu * nu;
   PolyCoef<R> c;
-  c.c0 = ((R)1 + B * T) / w;
-  c.c1 = A1 / w;
-  c.c2 = A2 / w;
+  c.c0 = m_div((R)1 + B * T, w);
+  c.c1 = m_div(A1, w);
+  c.c2 = m_div(A2, w);
   return c;
 }
 
@@ -258,16 +262,17 @@ template <class R>
 __device__ __forceinline__ PolyCoef<R> dynamic_poly(R alpha, R beta, R l2f, R T, R nu1sq,
                                                     R nu2sq, R eta1, R eta2sq) {
   const R omb = (R)1 - beta;
-  const R w = m_exp2(omb * l2f) / alpha;
-  const R A1 = (beta - (R)1) / (R)2 + eta1 * w / (R)2;
-  const R A2 = omb * omb / (R)12 + (omb - eta1 * w) / (R)4 +
-               ((R)4 * nu1sq + (R)3 * (eta2sq - (R)3 * eta1 * eta1)) / (R)24 * w * w;
-  const R B = (omb * omb / (R)24 + w * beta * eta1 / (R)4 +
-               ((R)2 * nu2sq - (R)3 * eta2sq) / (R)24 * w * w) / (w * w);
+  const R w = m_div(m_exp2(omb * l2f), alpha);
+  const R A1 = m_divc(beta - (R)1, 2.0) + m_divc(eta1 * w, 2.0);
+  const R A2 = m_divc(omb * omb, 12.0) + m_divc(omb - eta1 * w, 4.0) +
+               m_divc((R)4 * nu1sq + (R)3 * (eta2sq - (R)3 * eta1 * eta1), 24.0) * w * w;
+  const R B = m_div(m_divc(omb * omb, 24.0) + m_divc(w * beta * eta1, 4.0) +
+                        m_divc((R)2 * nu2sq - (R)3 * eta2sq, 24.0) * w * w,
+                    w * w);
   PolyCoef<R> c;
-  c.c0 = ((R)1 + B * T) / w;
-  c.c1 = A1 / w;
-  c.c2 = A2 / w;
+  c.c0 = m_div((R)1 + B * T, w);
+  c.c1 = m_div(A1, w);
+  c.c2 = m_div(A2, w);
   return c;
 }
 
