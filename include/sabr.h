@@ -142,6 +142,37 @@ sabr_status sabr_mc_price_noalloc(sabr_model model, const double* params,
                                   sabr_precision prec, void* cuda_stream);
 
 /* ------------------------------------------------------------------------
+ * sabr_mc_cliquet -- Monte Carlo price of a cliquet on the forward, Sec. 6.3
+ * eqs. (eq_cliquet) and (cliquet_global), on the paths of sabr_mc_price
+ * (same scheme, absorption and Philox streams; the reset dates are inserted
+ * into the step grid).  Reset dates d_i = i T / n_resets, i = 1..n_resets;
+ * the payoff is
+ *     g = sum_{i=2..n_resets} max(min(R_i, cap_local), floor_local),
+ *     R_i = F(d_i) / F(d_{i-1}) - 1,
+ *     price = discount * E[max(floor_global, min(cap_global, g))].
+ * The printed global formula, max(C_g, min(F_g, .)), is the constant C_g
+ * whenever F_g <= C_g; the limits are taken in the order that makes
+ * floor_global a floor.  A path absorbed before d_{i-1} adds R_i = 0.
+ *   params       host, double[10], as sabr_mc_price
+ *   T            final reset date (years), > 0; n_resets in [2, 64]
+ *   floor_local <= cap_local, floor_global <= cap_global (pass +-1e300 for
+ *                no global limits)
+ *   price_out    device, double[1]; stderr_out device double[1] or NULL
+ * Asynchronous on cuda_stream; device scratch is stream-ordered
+ * (cudaMallocAsync / cudaFreeAsync).  EINVAL for bad sizes or limits, more
+ * than 8192 time steps, or parameters violating rho(t) in [-1,1],
+ * nu(t) > 0 on [0, T].
+ * ------------------------------------------------------------------------ */
+sabr_status sabr_mc_cliquet(sabr_model model, const double* params, double fwd,
+                            double T, int32_t n_resets, double floor_local,
+                            double cap_local, double floor_global,
+                            double cap_global, double discount,
+                            int64_t n_paths, double steps_per_year,
+                            uint64_t seed, double* price_out,
+                            double* stderr_out, sabr_precision prec,
+                            void* cuda_stream);
+
+/* ------------------------------------------------------------------------
  * Calibration problems (Sec. 3 eqs. (error_calibrate_individual_relativo),
  * (error_calibrate_relativo); Sec. 5).  All arrays in a problem are HOST
  * memory and are copied by the call that receives them.

@@ -10,4 +10,4 @@ from . import capi  # noqa: F401
 from .capi import (COST_MC_PRICE, COST_VOL, DYN_I, DYN_II, EXPANDED, FP32, FP64, HAGAN,  # noqa: F401
                    OBLOJ, SabrError)
 from .api import (CalibrationProblem, CalibrationResult, Plan, Server, calibrate, calibrate_batch,  # noqa: F401
-                  implied_vol, mc_price)
+                  implied_vol, mc_cliquet, mc_price)

@@ -72,6 +72,22 @@ def mc_price(model, params, fwd, T, K, is_call=None, discount=None, n_paths=1 <<
     return price, se
 
 
+def mc_cliquet(model, params, fwd, T, n_resets, floor_local, cap_local, floor_global=-1e300, cap_global=1e300,
+               discount=1.0, n_paths=1 << 20, steps_per_year=250.0, seed=0, prec=FP32, stream=None, device="cuda"):
+    """Monte Carlo cliquet price and standard error (float64 CUDA tensors of one element)."""
+    lib = capi.load()
+    price = torch.empty(1, dtype=torch.float64, device=device)
+    se = torch.empty(1, dtype=torch.float64, device=device)
+    p = _params10(params, model)
+    st = lib.sabr_mc_cliquet(model, p.ctypes.data_as(capi.PD), float(fwd), float(T), int(n_resets),
+                             float(floor_local), float(cap_local), float(floor_global), float(cap_global),
+                             float(discount), int(n_paths), float(steps_per_year), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                             ctypes.c_void_p(price.data_ptr()), ctypes.c_void_p(se.data_ptr()), prec,
+                             _stream_handle(stream))
+    capi.check(st, "sabr_mc_cliquet")
+    return price, se
+
+
 @dataclass
 class CalibrationProblem:
     """One calibration problem: quotes, model and SA settings (host data)."""

@@ -72,6 +72,8 @@ SIGNATURES = {
                               c_void_p, c_void_p, c_int, c_void_p]),
     "sabr_mc_price_noalloc": (c_int, [c_int, PD, c_double, PD, PD, PI8, PD, c_int64, c_int64, c_double,
                                       c_uint64, c_void_p, c_void_p, c_int, c_void_p]),
+    "sabr_mc_cliquet": (c_int, [c_int, PD, c_double, c_double, c_int32, c_double, c_double, c_double, c_double,
+                                c_double, c_int64, c_double, c_uint64, c_void_p, c_void_p, c_int, c_void_p]),
     "sabr_calibrate": (c_int, [ctypes.POINTER(Problem), ctypes.POINTER(Bounds), ctypes.POINTER(Cooling),
                                c_uint64, ctypes.POINTER(Result), c_void_p]),
     "sabr_calibrate_batch": (c_int, [c_int32, ctypes.POINTER(Problem), ctypes.POINTER(Bounds),

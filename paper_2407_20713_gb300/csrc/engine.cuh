@@ -8,7 +8,11 @@
 
 namespace sabr {
 
-constexpr int kSaBlock = 256;  // threads per SA block
+constexpr int kSaBlock = 256;   // threads per SA block (server, init, finalize)
+// Threads per block of the plans' level kernel: small blocks spread a
+// batch's chains evenly over the 152 SMs (14 resident per SM at <= 72
+// registers), where 256-thread blocks leave a partly filled second wave.
+constexpr int kLevelBlock = 64;
 constexpr int kStateLen = 12;  // restart x[10], restart f, T0
 
 // One problem of a batch, as the kernels see it (all pointers device).
@@ -49,6 +53,12 @@ struct ProblemDev {
   sabr_result* result;
 };
 
+// The four per-quote inputs of the static formulas, packed so that one
+// 16-byte (FP32) shared-memory load fetches a quote.
+template <class R> struct __align__(16) QuotePack {
+  R lfk, l2kf, T, w;
+};
+
 // Quote tables of one problem staged in shared memory.
 template <class R> struct SmemQuotes {
   const R* lfk;
@@ -58,6 +68,7 @@ template <class R> struct SmemQuotes {
   const R* w;
   const int* mat;
   const R* mT;
+  const QuotePack<R>* pack;  // (lfk, l2kf, T, w) per quote
 };
 
 // Double-float number hi + lo (|lo| <= ulp(hi)/2): sums of FP32 terms carried
@@ -124,6 +135,43 @@ __device__ __forceinline__ DF lanes_sum(float v, int G, unsigned gmask) {
   return s;
 }
 
+// Per-maturity polynomials of a Case II point into coef[3 j ..]: nu1^2,
+// nu2^2, eta1 by one lane per maturity; then eta2^2 of each maturity by all
+// G lanes, which split its quadrature nodes and sum them by a fixed-order
+// butterfly (every lane gets the same total).
+template <class R>
+__device__ __forceinline__ void case2_group_coef(const R* xp, int n_mats, R l2f, const SmemQuotes<R>& sq, R* coef,
+                                                 int lane, int G, unsigned gmask) {
+  {
+    const R rho0 = (R)xp[2], nu0 = (R)xp[3], dr = (R)xp[6], dn = (R)xp[7];
+    for (int j = lane; j < n_mats; j += G) {
+      const R T = sq.mT[j];
+      R o3[3];
+      case2_single<R>(rho0, nu0, (R)xp[4] * T, (R)xp[5] * T, dr, dn, (R)xp[8] * T, (R)xp[9] * T, o3);
+      coef[3 * j + 0] = o3[0];
+      coef[3 * j + 1] = o3[1];
+      coef[3 * j + 2] = o3[2];
+    }
+    __syncwarp(gmask);
+    for (int j = 0; j < n_mats; ++j) {
+      const R T = sq.mT[j];
+      const R A = (R)xp[4] * T, B = (R)xp[5] * T, Qr = (R)xp[8] * T, Qn = (R)xp[9] * T;
+      const int nodes = case2_panels<R>(A, B) * Tr<R>::kGauss;
+      R part = (R)0;
+      for (int k = lane; k < nodes; k += G)
+        part += case2_eta2_node<R>(k, nodes / Tr<R>::kGauss, rho0, nu0, A, B, dr, dn, Qr, Qn);
+      for (int off = G >> 1; off > 0; off >>= 1) part += __shfl_xor_sync(gmask, part, off);
+      if (lane == (j & (G - 1))) {
+        const PolyCoef<R> c = dynamic_poly<R>((R)xp[0], (R)xp[1], l2f, T, coef[3 * j + 0], coef[3 * j + 1],
+                                              coef[3 * j + 2], part);
+        coef[3 * j + 0] = c.c0;
+        coef[3 * j + 1] = c.c1;
+        coef[3 * j + 2] = c.c2;
+      }
+    }
+  }
+}
+
 // Cost of point xp evaluated by the G lanes of one chain group.  Lane `lane`
 // takes quotes lane, lane+G, ...; per-lane partial sums are combined by
 // lanes_sum.
@@ -136,11 +184,12 @@ __device__ __forceinline__ typename CostOf<R>::T group_cost(const R* xp, int n_q
   R acc = (R)0;
   if (MODEL == SABR_HAGAN || MODEL == SABR_OBLOJ) {
     const StaticConst<R> sc = static_setup<R>(xp);
+#pragma unroll 4
     for (int q = lane; q < n_quotes; q += G) {
-      const R v = (MODEL == SABR_HAGAN)
-                      ? vol_hagan<R>(sc, sq.lfk[q], sq.l2kf[q], sq.T[q])
-                      : vol_obloj<R>(sc, sq.lfk[q], sq.l2kf[q], sq.l2k[q], sq.T[q]);
-      const R r = resid(v, sq.w[q]);
+      const QuotePack<R> qp = sq.pack[q];
+      const R v = (MODEL == SABR_HAGAN) ? vol_hagan<R>(sc, qp.lfk, qp.l2kf, qp.T)
+                                        : vol_obloj<R>(sc, qp.lfk, qp.l2kf, sq.l2k[q], qp.T);
+      const R r = resid(v, qp.w);
       acc += r * r;
     }
   } else if (MODEL == SABR_EXPANDED) {
@@ -154,11 +203,15 @@ __device__ __forceinline__ typename CostOf<R>::T group_cost(const R* xp, int n_q
       acc += r * r;
     }
   } else {
-    for (int j = lane; j < n_mats; j += G) {
-      const PolyCoef<R> c = dynamic_coef<R, MODEL == SABR_DYN_II>(xp, l2f, sq.mT[j]);
-      coef[3 * j + 0] = c.c0;
-      coef[3 * j + 1] = c.c1;
-      coef[3 * j + 2] = c.c2;
+    if (MODEL == SABR_DYN_I) {
+      for (int j = lane; j < n_mats; j += G) {
+        const PolyCoef<R> c = dynamic_coef<R, false>(xp, l2f, sq.mT[j]);
+        coef[3 * j + 0] = c.c0;
+        coef[3 * j + 1] = c.c1;
+        coef[3 * j + 2] = c.c2;
+      }
+    } else {
+      case2_group_coef<R>(xp, n_mats, l2f, sq, coef, lane, G, gmask);
     }
     __syncwarp(gmask);
     for (int q = lane; q < n_quotes; q += G) {
@@ -174,5 +227,6 @@ __device__ __forceinline__ typename CostOf<R>::T group_cost(const R* xp, int n_q
   }
   return lanes_sum(acc, G, gmask);
 }
+
 
 }  // namespace sabr

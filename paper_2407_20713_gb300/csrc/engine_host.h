@@ -31,13 +31,14 @@ size_t init_smem_bytes(const HostProblem& h);
 // Lays out one problem's device region at [off0, end) of an arena: its
 // quotes, schedule, start point, chain state and block partials, filling d.
 // img == nullptr performs a dry run (offsets only).  Returns end.
+// `block`: threads per level block (chains per block = block / G).
 size_t formula_layout(const HostProblem& h, int G, unsigned char* img, unsigned char* base, size_t off0,
-                      ProblemDev& d, sabr_result* dres);
+                      ProblemDev& d, sabr_result* dres, int block = kSaBlock);
 
 // Kernel launches for (prec, model).
 void set_engine_smem(int prec, int model, size_t bytes);
 void launch_init(int prec, int model, const ProblemDev* probs, const int* plist, int n, size_t smem, cudaStream_t s);
-void launch_level(int prec, int model, const ProblemDev* probs, const int2* bmap, int blocks, int level, size_t smem,
+void launch_level(int prec, int model, const ProblemDev* probs, const int4* bmap, int blocks, int level, size_t smem,
                   cudaStream_t s);
 void launch_persistent(int prec, int model, const ProblemDev* probs, const int4* work, const int* n_work, int grid,
                        size_t smem, cudaStream_t s);

@@ -15,7 +15,7 @@ namespace sabr {
 // Kernels
 // ---------------------------------------------------------------------------
 struct McSmem {
-  size_t tab, smat, q0, nq, slot, K, call, wacc, total;
+  size_t tab, land, q0, nq, slot, K, call, wacc, total;
 };
 
 template <class R>
@@ -30,7 +30,7 @@ __host__ __device__ inline McSmem mc_smem_layout(int n_steps, int n_quotes, int 
   L.wacc = take(sizeof(double) * kMcWarps * n_slots * 32);
   L.tab = take(sizeof(StepCoef<R>) * n_steps);
   L.K = take(sizeof(R) * n_quotes);
-  L.smat = take(sizeof(int) * n_steps);
+  L.land = take(sizeof(int) * n_mats);
   L.q0 = take(sizeof(int) * n_mats);
   L.nq = take(sizeof(int) * n_mats);
   L.slot = take(sizeof(int) * n_mats);
@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kMcBlock) mc_paths_kernel(McDev P, const doubl
   double* wacc = (double*)(smem + L.wacc);
   StepCoef<R>* tab = (StepCoef<R>*)(smem + L.tab);
   R* sK = (R*)(smem + L.K);
-  int* smat = (int*)(smem + L.smat);
+  int* land = (int*)(smem + L.land);
   int* s_q0 = (int*)(smem + L.q0);
   int* s_nq = (int*)(smem + L.nq);
   int* s_slot = (int*)(smem + L.slot);
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(kMcBlock) mc_paths_kernel(McDev P, const doubl
   for (int i = 0; i < kMaxD; ++i) p[i] = set_params[(size_t)set * kMaxD + i];
   const int nv = P.n_slots * 32;
   for (int i = threadIdx.x; i < kMcWarps * nv; i += blockDim.x) wacc[i] = 0.0;
-  build_steps<R>(P, p, tab, smat);
+  build_steps<R>(P, p, tab, land);
   for (int q = threadIdx.x; q < P.n_quotes; q += blockDim.x) {
     sK[q] = (R)P.K[q];
     scall[q] = P.is_call[q];
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kMcBlock) mc_paths_kernel(McDev P, const doubl
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5;
-  simulate_paths<R>(P, p, tab, smat, s_q0, s_nq, s_slot, sK, scall,
+  simulate_paths<R>(P, p, tab, land, s_q0, s_nq, s_slot, sK, scall,
                     (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x,
                     wacc + (size_t)warp * nv);
   __syncthreads();
@@ -266,16 +266,31 @@ void mc_fill_image(const McHost& h, unsigned char* host_img, unsigned char* dev_
   *disc = (double*)put(h.disc.data(), 8 * h.disc.size());
 }
 
-int mc_blocks_per_set(const McHost& h, int n_sets) {
-  const int64_t target = 152 * 8;  // resident 128-thread blocks across the GPU
-  int64_t per = std::max<int64_t>(1, target / std::max(1, n_sets));
-  const int64_t by_paths = (h.n_paths + kMcBlock - 1) / kMcBlock;
-  return (int)std::max<int64_t>(1, std::min(per, by_paths));
-}
-
 template <class R>
 static void set_mc_smem(size_t bytes) {
   cudaFuncSetAttribute(mc_paths_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Blocks per parameter set: the resident 128-thread blocks of the GPU (at
+// most 8 per SM, 1216 in all) shared among the sets, and no more than the
+// paths need (each thread takes kMcPathsPerThread paths at a time); the
+// kernel's grid-stride loop covers the rest, so there is no partly filled
+// second wave.
+int mc_blocks_per_set(const McHost& h, int n_sets) {
+  int per_sm = 8;
+  if (h.prec == SABR_FP64) {
+    set_mc_smem<double>(h.smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mc_paths_kernel<double>, kMcBlock, h.smem);
+  } else {
+    set_mc_smem<float>(h.smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mc_paths_kernel<float>, kMcBlock, h.smem);
+  }
+  per_sm = std::min(std::max(per_sm, 1), 8);
+  const int64_t target = 152 * (int64_t)per_sm;
+  const int64_t per = std::max<int64_t>(1, target / std::max(1, n_sets));
+  const int64_t per_block = (int64_t)kMcBlock * kMcPathsPerThread;
+  const int64_t by_paths = (h.n_paths + per_block - 1) / per_block;
+  return (int)std::max<int64_t>(1, std::min(per, by_paths));
 }
 
 sabr_status mc_launch(const McHost& h, const McDev& d, const double* set_params, const int* set_valid, int n_sets,

@@ -20,6 +20,7 @@
 // nothing needs clearing.  Calls whose work overlaps on the GPU (different
 // streams, or different host threads on the same device without ordering)
 // race on the array.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -88,7 +89,11 @@ extern "C" sabr_status sabr_mc_price_noalloc(sabr_model model, const double* par
   SABR_TRY(mc_prepare(model, fwd, T, K, is_call, discount, n, n_paths, steps_per_year, seed, prec, h));
   if (!noalloc_feasible(model, params, h.Tmax))
     return fail(SABR_EINVAL, "parameters violate rho(t) in [-1,1], nu(t) > 0");
-  const int bps = mc_blocks_per_set(h, 1);
+  // a fixed grid (at most 1216 blocks), independent of the occupancy the
+  // pricing kernel reaches, so the scratch bound below is a property of the
+  // problem alone
+  const int64_t per_block = (int64_t)kMcBlock * kMcPathsPerThread;
+  const int bps = (int)std::min<int64_t>(1216, (h.n_paths + per_block - 1) / per_block);
   const size_t img = mc_image_bytes(h);
   const size_t params_off = (img + 255) & ~(size_t)255;
   const size_t part_off = params_off + 256;

@@ -47,9 +47,35 @@ __device__ __forceinline__ SmemQuotes<R> stage_quotes(const ProblemDev& P, unsig
   }
   for (int j = tid; j < M; j += nthreads) mT[j] = ((const R*)P.m_T)[j];
   unsigned char* e = (unsigned char*)(mat + Q);
-  *end = (unsigned char*)(((uintptr_t)e + 15) & ~(uintptr_t)15);
-  SmemQuotes<R> sq{lfk, l2kf, l2k, T, w, mat, mT};
+  QuotePack<R>* pack = (QuotePack<R>*)(((uintptr_t)e + 15) & ~(uintptr_t)15);
+  for (int i = tid; i < Q; i += nthreads) {
+    QuotePack<R> qp;
+    qp.lfk = ((const R*)P.q_lfk)[i];
+    qp.l2kf = ((const R*)P.q_l2kf)[i];
+    qp.T = ((const R*)P.q_T)[i];
+    qp.w = ((const R*)P.q_w)[i];
+    pack[i] = qp;
+  }
+  *end = (unsigned char*)(pack + Q);
+  SmemQuotes<R> sq{lfk, l2kf, l2k, T, w, mat, mT, pack};
   return sq;
+}
+
+// Lexicographic minimum of (f, i): the smaller f, then the smaller index, so
+// the result does not depend on the order of merging.
+__device__ __forceinline__ void argmin_merge(double& f, int& i, double f2, int i2) {
+  if (f2 < f || (f2 == f && i2 < i)) {
+    f = f2;
+    i = i2;
+  }
+}
+__device__ __forceinline__ void warp_argmin(double& f, int& i) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double f2 = __shfl_xor_sync(0xffffffffu, f, off);
+    const int i2 = __shfl_xor_sync(0xffffffffu, i, off);
+    argmin_merge(f, i, f2, i2);
+  }
 }
 
 template <int MODEL> struct Dim {
@@ -154,22 +180,24 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
     s_hi[i] = (R)P.hi[i];
   }
   __syncthreads();
-  R x[D], bx[D];
+  R x[D];
 #pragma unroll
   for (int i = 0; i < D; ++i) x[i] = (R)P.state[i];
   using C = typename CostOf<R>::T;
   C fcur = cost_from(P.state[kMaxD], C{});
   C bf = fcur;
   const float inv_Tk = (float)(1.0 / Tk);
+  // the chain's best point lives in its chain_bx row (written by lane 0 on
+  // each improvement), not in registers
   R* cbx = (R*)P.chain_bx + (size_t)chain * kMaxD;
   if (active) {
     if (level == 0) {
+      if (lane == 0) {
 #pragma unroll
-      for (int i = 0; i < D; ++i) bx[i] = x[i];
+        for (int i = 0; i < kMaxD; ++i) cbx[i] = i < D ? x[i] : (R)0;
+      }
     } else {
       bf = cost_from(P.chain_bf[chain], C{});
-#pragma unroll
-      for (int i = 0; i < D; ++i) bx[i] = cbx[i];
     }
   }
   unsigned ev = 0, ac = 0;  // per level: at most chain_len each
@@ -231,8 +259,10 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
       if (cost_is_nan(fp)) continue;
       if (cost_less(fp, bf)) {
         bf = fp;
+        if (lane == 0) {
 #pragma unroll
-        for (int i = 0; i < D; ++i) bx[i] = xp[i];
+          for (int i = 0; i < D; ++i) cbx[i] = xp[i];
+        }
       }
       const auto delta = cost_delta(fp, fcur);
       if (delta <= 0 || metropolis(u[D], delta, inv_Tk, Tk)) {
@@ -244,8 +274,6 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
     }
     if (lane == 0) {
       P.chain_bf[chain] = cost_to_double(bf);
-#pragma unroll
-      for (int i = 0; i < kMaxD; ++i) cbx[i] = i < D ? bx[i] : (R)0;
       if (level == 0) {
         P.chain_ev[chain] = ev;
         P.chain_ac[chain] = ac;
@@ -262,32 +290,40 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
   }
   __syncthreads();
 
-  if (threadIdx.x == 0) {
-    // block argmin of the final states; lowest chain index on a tie
-    int best = 0;
-    double fb = red_f[0];
-    for (int c = 1; c < cpb; ++c)
-      if (red_f[c] < fb) {
-        fb = red_f[c];
-        best = c;
-      }
-    P.part_f[bm.y] = fb;
-    P.part_c[bm.y] = bm.y * cpb + best;
-    for (int i = 0; i < kMaxD; ++i) P.part_x[(size_t)bm.y * kMaxD + i] = (double)red_x[best * kMaxD + i];
-    __threadfence();
-    const unsigned ticket = atomicAdd(P.arrive, 1u);
-    if (ticket == (unsigned)(P.n_blocks - 1)) {
-      // last block of this problem: restart point of the next level
+  // block argmin of the final states (lowest chain index on a tie), by warp 0
+  __shared__ int s_last;
+  if (threadIdx.x < 32) {
+    double fb = INFINITY;
+    int best = 0x7fffffff;
+    for (int c = threadIdx.x; c < cpb; c += 32) argmin_merge(fb, best, red_f[c], c);
+    warp_argmin(fb, best);
+    if (threadIdx.x == 0) {
+      P.part_f[bm.y] = fb;
+      P.part_c[bm.y] = bm.y * cpb + best;
+      for (int i = 0; i < kMaxD; ++i) P.part_x[(size_t)bm.y * kMaxD + i] = (double)red_x[best * kMaxD + i];
       __threadfence();
-      int bb = 0;
-      double f = __ldcg(&P.part_f[0]);
-      for (int b = 1; b < P.n_blocks; ++b) {
-        const double v = __ldcg(&P.part_f[b]);
-        if (v < f) {
-          f = v;
-          bb = b;
-        }
-      }
+      const unsigned ticket = atomicAdd(P.arrive, 1u);
+      s_last = ticket == (unsigned)(P.n_blocks - 1);
+    }
+  }
+  __syncthreads();
+  if (s_last) {
+    // last block of this problem: the restart point of the next level is the
+    // argmin over the block minima (lowest block on a tie), by every thread
+    __shared__ double s_wf[kSaBlock / 32];
+    __shared__ int s_wb[kSaBlock / 32];
+    __threadfence();
+    double f = INFINITY;
+    int bb = 0x7fffffff;
+    for (int b = threadIdx.x; b < P.n_blocks; b += blockDim.x) argmin_merge(f, bb, __ldcg(&P.part_f[b]), b);
+    warp_argmin(f, bb);
+    if ((threadIdx.x & 31) == 0) {
+      s_wf[threadIdx.x >> 5] = f;
+      s_wb[threadIdx.x >> 5] = bb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) argmin_merge(f, bb, s_wf[w], s_wb[w]);
       for (int i = 0; i < kMaxD; ++i) P.state[i] = __ldcg(&P.part_x[(size_t)bb * kMaxD + i]);
       P.state[kMaxD] = f;
       *P.arrive = 0u;
@@ -295,31 +331,31 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
   }
 }
 
-template <class R, int MODEL>
-__global__ void __launch_bounds__(kSaBlock, sizeof(R) == 4 ? 3 : 1) sa_level_kernel(const ProblemDev* __restrict__ probs,
-                                                           const int2* __restrict__ bmap, int level) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ ProblemDev P;
-  const int2 bm = bmap[blockIdx.x];
-  load_problem(probs, bm.x, &P);
-  if (level >= P.n_levels) return;
-  sa_level_block<R, MODEL>(P, bm.y, level, smem);
-}
+// One temperature level for a list of (problem, block) work items.
+// Plans launch one block per item with `level` >= 0 (the level of the
+// launch); the server launches a fixed grid that strides over a work list
+// read from device memory (n_work != nullptr), each item carrying its own
+// level in .z (level < 0), so that one captured launch serves every step
+// whatever its mix of requests.  Both use this one kernel, so a problem's
+// arithmetic is the same machine code in a plan and in the server.
+// Register budget: the static formulas' quote loop runs four quotes at a
+// time (up to 128 registers); the polynomial and dynamic models keep 80.
+template <class R, int MODEL> struct LevelMinBlocks {
+  static constexpr int value = sizeof(R) == 8 ? 1 : (MODEL == SABR_HAGAN || MODEL == SABR_OBLOJ ? 2 : 3);
+};
 
-// Grid-stride form for the server: work[w] = (problem, block, level) for
-// w < *n_work, read from device memory so one captured launch serves every
-// step whatever its mix of requests.
 template <class R, int MODEL>
-__global__ void __launch_bounds__(kSaBlock, sizeof(R) == 4 ? 3 : 1) sa_level_persistent(const ProblemDev* __restrict__ probs,
-                                                               const int4* __restrict__ work,
-                                                               const int* __restrict__ n_work) {
+__global__ void __launch_bounds__(kSaBlock, (LevelMinBlocks<R, MODEL>::value))
+    sa_level_kernel(const ProblemDev* __restrict__ probs, const int4* __restrict__ work,
+                    const int* __restrict__ n_work, int n_items, int level) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ ProblemDev P;
-  const int nw = *n_work;
+  const int nw = n_work ? *n_work : n_items;
   for (int w = blockIdx.x; w < nw; w += gridDim.x) {
     const int4 it = work[w];
+    const int lv = level >= 0 ? level : it.z;
     load_problem(probs, it.x, &P);
-    if (it.z < P.n_levels) sa_level_block<R, MODEL>(P, it.y, it.z, smem);
+    if (lv < P.n_levels) sa_level_block<R, MODEL>(P, it.y, lv, smem);
     __syncthreads();
   }
 }
@@ -464,19 +500,21 @@ static int next_pow2(int v) {
   return p;
 }
 
-// About eight quotes per lane, widened while the whole batch would not fill
-// the GPU (fewer than 64k threads) and quotes remain to split; the dynamic
-// models take at least one lane per maturity.
+// About 24 quotes per lane (a lane runs its quote loop four quotes at a
+// time), widened while the batch has fewer than 152 x 256 threads and quotes
+// remain to split; the dynamic models take at least one lane per maturity.
 int choose_lanes(int n_quotes, int n_mats, int model, long long batch_chains) {
   if (const char* e = std::getenv("SABR_LANES")) {
     int g = std::atoi(e);
     if (g >= 1 && g <= 32 && (g & (g - 1)) == 0) return g;
   }
-  int G = next_pow2((n_quotes + 7) / 8);
+  // fewer lanes repeat the per-proposal work (Philox, proposal,
+  // Metropolis, lane sum) less often
+  int G = next_pow2((n_quotes + 23) / 24);
   if (model == SABR_DYN_I || model == SABR_DYN_II) G = std::max(G, next_pow2(n_mats));
   G = std::min(G, 32);
   const int cap = std::min(32, next_pow2(n_quotes));
-  while (G < cap && batch_chains * G < 65536) G <<= 1;
+  while (G < cap && batch_chains * G < 152 * 256) G <<= 1;
   return G;
 }
 
@@ -484,7 +522,7 @@ size_t level_smem_bytes(int prec, int model, int Q, int M, int cpb) {
   const size_t rs = prec == SABR_FP64 ? 8 : 4;
   const size_t cm = (model == SABR_DYN_I || model == SABR_DYN_II) ? (size_t)M : 0;
   size_t b = (5 * (size_t)Q + M) * rs + 4 * (size_t)Q;
-  b = align_up(b, 16);
+  b = align_up(b, 16) + 4 * rs * (size_t)Q;  // QuotePack table
   b += (size_t)cpb * 3 * cm * rs + 16 * rs;
   b = align_up(b, 16) + 16;
   b += (size_t)cpb * 8 + (size_t)cpb * kMaxD * rs;
@@ -562,7 +600,7 @@ sabr_status formula_prepare(const sabr_problem& pr, const sabr_bounds& b, const 
 }
 
 size_t formula_layout(const HostProblem& h, int G, unsigned char* img, unsigned char* base, size_t off0,
-                      ProblemDev& d, sabr_result* dres) {
+                      ProblemDev& d, sabr_result* dres, int block) {
   size_t o = off0;
   auto take = [&](size_t bytes) {
     o = align_up(o, 256);
@@ -585,7 +623,7 @@ size_t formula_layout(const HostProblem& h, int G, unsigned char* img, unsigned 
   d.n_levels = h.n_levels;
   d.chain_len = h.chain_len;
   d.G = G;
-  d.cpb = kSaBlock / G;
+  d.cpb = block / G;
   d.n_blocks = (h.n_chains + d.cpb - 1) / d.cpb;
   d.fwd = h.fwd;
   d.l2f = std::log2(h.fwd);
@@ -675,7 +713,6 @@ size_t formula_layout(const HostProblem& h, int G, unsigned char* img, unsigned 
 template <class R, int MODEL>
 static void set_smem_one(size_t bytes) {
   cudaFuncSetAttribute(sa_level_kernel<R, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  cudaFuncSetAttribute(sa_level_persistent<R, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   cudaFuncSetAttribute(sa_init_kernel<R, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
@@ -708,14 +745,15 @@ void launch_init(int prec, int model, const ProblemDev* probs, const int* plist,
   SABR_DISPATCH(prec, model, (sa_init_kernel<R, M><<<n, 32, smem, s>>>(probs, plist)));
 }
 
-void launch_level(int prec, int model, const ProblemDev* probs, const int2* bmap, int blocks, int level, size_t smem,
+void launch_level(int prec, int model, const ProblemDev* probs, const int4* bmap, int blocks, int level, size_t smem,
                   cudaStream_t s) {
-  SABR_DISPATCH(prec, model, (sa_level_kernel<R, M><<<blocks, kSaBlock, smem, s>>>(probs, bmap, level)));
+  SABR_DISPATCH(prec, model,
+                (sa_level_kernel<R, M><<<blocks, kLevelBlock, smem, s>>>(probs, bmap, nullptr, blocks, level)));
 }
 
 void launch_persistent(int prec, int model, const ProblemDev* probs, const int4* work, const int* n_work, int grid,
                        size_t smem, cudaStream_t s) {
-  SABR_DISPATCH(prec, model, (sa_level_persistent<R, M><<<grid, kSaBlock, smem, s>>>(probs, work, n_work)));
+  SABR_DISPATCH(prec, model, (sa_level_kernel<R, M><<<grid, kSaBlock, smem, s>>>(probs, work, n_work, 0, -1)));
 }
 
 void launch_finalize(int prec, int model, const ProblemDev* probs, const int* plist, int n, cudaStream_t s) {
@@ -725,7 +763,7 @@ void launch_finalize(int prec, int model, const ProblemDev* probs, const int* pl
 int persistent_blocks_per_sm(int prec, int model, size_t smem) {
   int nb = 1;
   SABR_DISPATCH(prec, model,
-                (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sa_level_persistent<R, M>, kSaBlock, smem)));
+                (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sa_level_kernel<R, M>, kSaBlock, smem)));
   return nb < 1 ? 1 : nb;
 }
 
@@ -735,7 +773,7 @@ struct LaunchGroup {
   int total_blocks = 0;
   int max_levels = 0;
   size_t smem_level = 0, smem_init = 0;
-  int2* d_bmap = nullptr;
+  int4* d_bmap = nullptr;
   int* d_plist = nullptr;
 };
 
@@ -858,7 +896,7 @@ static sabr_status build_plan(int32_t n, const sabr_problem* problems, const sab
   for (int i = 0; i < nf; ++i) {
     lanes[i] = choose_lanes(hp[i].n_quotes, hp[i].n_mats, hp[i].model, batch_chains);
     f_off[i] = align_up(o, 256);
-    o = formula_layout(hp[i], lanes[i], nullptr, nullptr, f_off[i], pd[i], nullptr);
+    o = formula_layout(hp[i], lanes[i], nullptr, nullptr, f_off[i], pd[i], nullptr, kLevelBlock);
   }
   for (size_t k = 0; k < p->mc.size(); ++k) mc_off[k] = take(mcsa_arena_bytes(p->mc[k]));
   for (int i = 0; i < nf; ++i) {
@@ -881,7 +919,7 @@ static sabr_status build_plan(int32_t n, const sabr_problem* problems, const sab
   }
   std::vector<size_t> bmap_off(p->groups.size()), plist_off(p->groups.size());
   for (size_t gi = 0; gi < p->groups.size(); ++gi) {
-    bmap_off[gi] = take(sizeof(int2) * p->groups[gi].total_blocks);
+    bmap_off[gi] = take(sizeof(int4) * p->groups[gi].total_blocks);
     plist_off[gi] = take(sizeof(int) * p->groups[gi].problems.size());
   }
   const size_t arena_bytes = align_up(o, 256);
@@ -894,17 +932,18 @@ static sabr_status build_plan(int32_t n, const sabr_problem* problems, const sab
   }
   unsigned char* base = (unsigned char*)p->arena;
   sabr_result* dres = (sabr_result*)(base + results_off);
-  for (int i = 0; i < nf; ++i) formula_layout(hp[i], lanes[i], img.data(), base, f_off[i], pd[i], dres + fidx[i]);
+  for (int i = 0; i < nf; ++i)
+    formula_layout(hp[i], lanes[i], img.data(), base, f_off[i], pd[i], dres + fidx[i], kLevelBlock);
   for (size_t k = 0; k < p->mc.size(); ++k) mcsa_layout(p->mc[k], img.data(), base, mc_off[k], dres + p->mc_index[k]);
   if (nf > 0) std::memcpy(img.data() + probs_off, pd.data(), sizeof(ProblemDev) * nf);
   for (size_t gi = 0; gi < p->groups.size(); ++gi) {
     LaunchGroup& g = p->groups[gi];
-    std::vector<int2> bm;
+    std::vector<int4> bm;
     for (int pi : g.problems)
-      for (int b = 0; b < pd[pi].n_blocks; ++b) bm.push_back(make_int2(pi, b));
-    std::memcpy(img.data() + bmap_off[gi], bm.data(), sizeof(int2) * bm.size());
+      for (int b = 0; b < pd[pi].n_blocks; ++b) bm.push_back(make_int4(pi, b, 0, 0));
+    std::memcpy(img.data() + bmap_off[gi], bm.data(), sizeof(int4) * bm.size());
     std::memcpy(img.data() + plist_off[gi], g.problems.data(), sizeof(int) * g.problems.size());
-    g.d_bmap = (int2*)(base + bmap_off[gi]);
+    g.d_bmap = (int4*)(base + bmap_off[gi]);
     g.d_plist = (int*)(base + plist_off[gi]);
     set_engine_smem(g.prec, g.model, std::max(g.smem_level, g.smem_init));
   }

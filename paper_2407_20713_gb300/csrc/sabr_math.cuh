@@ -28,7 +28,14 @@ template <> struct Tr<double> {
 
 __device__ __forceinline__ float m_exp(float x) { return expf(x); }
 __device__ __forceinline__ double m_exp(double x) { return exp(x); }
-__device__ __forceinline__ float m_exp2(float x) { return exp2f(x); }
+// FP32 2^x by the SFU instruction (PTX ex2.approx.ftz.f32, about 2 ulp;
+// results below 2^-126 flush to zero, which no caller reaches).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float m_exp2(float x) { return ex2_approx(x); }
 __device__ __forceinline__ double m_exp2(double x) { return exp2(x); }
 __device__ __forceinline__ float m_log(float x) { return logf(x); }
 __device__ __forceinline__ double m_log(double x) { return log(x); }
@@ -111,8 +118,10 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
     const uint32_t ma = 0xD2511F53u, mb = 0xCD9E8D57u;
-    const uint32_t ha = __umulhi(ma, c.x), la = ma * c.x;
-    const uint32_t hb = __umulhi(mb, c.z), lb = mb * c.z;
+    // each 32 x 32 -> 64-bit product in one wide multiply
+    const uint64_t pa = (uint64_t)ma * c.x, pb = (uint64_t)mb * c.z;
+    const uint32_t ha = (uint32_t)(pa >> 32), la = (uint32_t)pa;
+    const uint32_t hb = (uint32_t)(pb >> 32), lb = (uint32_t)pb;
     c = make_uint4(hb ^ c.y ^ k0, lb, ha ^ c.w ^ k1, la);
     k0 += 0x9E3779B9u;
     k1 += 0xBB67AE85u;
@@ -128,36 +137,34 @@ template <class R> __device__ __forceinline__ R u01(uint32_t w) {
 }
 
 // ---------------------------------------------------------------------------
-// z / x(z), eq. (equis):  x = ln((D + z - rho)/(1 - rho)),
+// z / x(z), eq. (equis):  x = ln u,  u = (D + z - rho)/(1 - rho),
 // D = sqrt(1 - 2 rho z + z^2) = sqrt((z - rho)^2 + (1 - rho)(1 + rho)).
-// Writing u for the log's argument, u - 1 = 2 z / (1 - z + D) exactly, whose
-// denominator is a sum of positive terms when z < 1; there x = log1p(u - 1)
-// unless u < 1/2, where u = (1 + rho) / (D - (z - rho)) is formed directly.
-// For z >= 1 the printed form has no cancellation.  omr = 1 - rho and
-// opr = 1 + rho are passed in, formed from the FP64 parameter.
+// Since (D + z - rho)(D - z + rho) = (1 - rho)(1 + rho), also
+// u = (1 + rho)/(D - z + rho); the first form has no cancellation for
+// z >= rho, the second none for z <= rho, so u is one division of selected
+// operands.  Near z = 0, ln u alone loses the relative accuracy of x, and
+// Goldberg's identity ln(1 + w) = w ln(u)/(u - 1) (u the rounded 1 + w) is
+// used with w = u - 1 = 2 z/(1 - z + D), i.e.
+//     z / x = (u - 1)(1 - z + D) / (2 ln u)     (z/w = (1 - z + D)/2),
+// and z / x = (1 - z + D)/2 when u rounds to 1.  Every lane runs the same
+// instructions whatever the sign and size of z (selects, no branches).
+// omr = 1 - rho and opr = 1 + rho are passed in, formed from the FP64
+// parameter.  The result is returned as a quotient zn / xd so callers fold
+// it into their own single division.
 // ---------------------------------------------------------------------------
 template <class R>
-__device__ __forceinline__ R x_of_z(R z, R rho, R omr, R opr) {
+__device__ __forceinline__ void z_over_x_parts(R z, R rho, R omr, R opr, R& zn, R& xd) {
   const R zr = z - rho;
   const R D = m_sqrt_pos(zr * zr + omr * opr);
-  if (z < (R)1) {
-    const R w = m_div((R)2 * z, (R)1 - z + D);
-    return (w >= (R)-0.5) ? m_log1p(w) : m_log(m_div(opr, D - zr));
-  }
-  return m_log(m_div(D + zr, omr));
-}
-
-// z/x(z) as a quotient zn/xd (1/1 at z = 0), so callers fold it into their
-// own single division.
-template <class R>
-__device__ __forceinline__ void z_over_x_parts(R z, R rho, R omr, R opr, R& zn, R& xd) {
-  if (z == (R)0) {
-    zn = (R)1;
-    xd = (R)1;
-  } else {
-    zn = z;
-    xd = x_of_z<R>(z, rho, omr, opr);
-  }
+  const bool low = z <= rho;
+  const R u = m_div(low ? opr : D + zr, low ? D - zr : omr);
+  const R L = m_log(u);
+  const R um1 = u - (R)1;
+  const R half_w_inv = ((R)1 - z + D) * (R)0.5;  // z / w
+  const bool near = z > (R)-0.5 && z < (R)0.5;
+  const bool one = um1 == (R)0;
+  zn = one ? half_w_inv : (near ? um1 * half_w_inv : z);
+  xd = one ? (R)1 : L;
 }
 
 template <class R>
@@ -464,6 +471,24 @@ __device__ __forceinline__ R case2_eta2_panel(int panel, int npanels, R rho0, R 
     acc += (R)kGaussRule<NG>.w[i] * ((R)1 - s) * G * G;
   }
   return (R)12 * h * acc;
+}
+
+// Node k of the eta2^2 rule on panel k / NG (the k % NG-th Gauss point):
+// its term 12 h w (1 - s) G(s)^2, so that eta2^2 is the sum over all
+// k < npanels * NG of these terms (lanes may share the nodes of one
+// maturity).
+template <class R>
+__device__ __forceinline__ R case2_eta2_node(int k, int npanels, R rho0, R nu0, R A, R B, R dr, R dn, R Qr,
+                                             R Qn) {
+  constexpr int NG = Tr<R>::kGauss;
+  const int panel = k / NG, i = k % NG;
+  R hi = (R)1;
+  for (int q = npanels - 1; q > panel; --q) hi *= (R)0.25;
+  const R lo = panel > 0 ? hi * (R)0.25 : (R)0;
+  const R c = (R)0.5 * (lo + hi), h = (R)0.5 * (hi - lo);
+  const R s = c + h * (R)kGaussRule<NG>.x[i];
+  const R G = case2_G<R>(s, rho0, nu0, A, B, dr, dn, Qr, Qn);
+  return (R)12 * h * (R)kGaussRule<NG>.w[i] * ((R)1 - s) * G * G;
 }
 
 // All four Case II functions at T (single thread).

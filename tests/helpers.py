@@ -41,3 +41,32 @@ def bachelier_call(f, K, T, sigma_n):
     s = sigma_n * np.sqrt(T)
     d = (f - K) / s
     return (f - K) * norm.cdf(d) + s * norm.pdf(d)
+
+
+# Exact law of the Sec. 6.3 cliquet when the forward is a geometric Brownian
+# motion (SABR with nu = 0, beta = 1): the local returns are i.i.d. with
+# 1 + R lognormal of mean 1.
+def clipped_return_pmf(sigma, dt, fl, cl, n_cells):
+    """Law of max(min(R, cl), fl) on the grid fl + j (cl - fl)/n_cells: atoms
+    at both ends, each cell's mass split between its two end nodes."""
+    s = sigma * np.sqrt(dt)
+    x = np.linspace(fl, cl, n_cells + 1)
+    cdf = norm.cdf((np.log1p(x) + 0.5 * s * s) / s)  # P(R <= x)
+    pmf = np.zeros(n_cells + 1)
+    cell = np.diff(cdf)
+    pmf[:-1] += 0.5 * cell
+    pmf[1:] += 0.5 * cell
+    pmf[0] += cdf[0]
+    pmf[-1] += 1.0 - cdf[-1]
+    return x, pmf
+
+
+def exact_gbm_cliquet(sigma, T, n_resets, fl, cl, fg, cg, n_cells=4000):
+    dt = T / n_resets
+    x, pmf = clipped_return_pmf(sigma, dt, fl, cl, n_cells)
+    tot = pmf
+    for _ in range(n_resets - 2):
+        tot = np.convolve(tot, pmf)
+    k = n_resets - 1
+    grid = k * fl + (cl - fl) / n_cells * np.arange(tot.size)
+    return float(np.sum(tot * np.clip(grid, fg, cg)))

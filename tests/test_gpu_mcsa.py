@@ -22,6 +22,10 @@ def _problem(model, lo, hi, prec, truth, **kw):
 @pytest.mark.parametrize("model,truth,lo,hi", [
     (sg.HAGAN, [0.25, 0.6, -0.3, 0.5], [0.25, 0.6, -0.9, 0.1], [0.25, 0.6, 0.5, 1.5]),
     (sg.DYN_I, [0.25, 0.8, -0.4, 0.6, 0.5, 0.8], [0.1, 0.8, -0.9, 0.1, 0.0, 0.0], [0.5, 0.8, 0.5, 1.5, 2.0, 2.0]),
+    # DSabr_II, the paper's Technique II model (Sec. 6.2): infeasible
+    # proposals (rho(t) or nu(t) out of range) are rejected on both sides
+    (sg.DYN_II, [0.25, 0.8, -0.4, 0.6, 0.5, 0.8, 0.05, 0.1, 0.1, 0.1],
+     [0.1, 0.8, -0.8, 0.2, 0.0, 0.0, -0.2, 0.0, -0.3, -0.3], [0.5, 0.8, 0.3, 1.2, 2.0, 2.0, 0.2, 0.3, 0.3, 0.3]),
 ])
 def test_fp64_mc_cost_trajectory_is_the_oracle_trajectory(model, truth, lo, hi):
     pb, mkt = _problem(model, lo, hi, sg.FP64, truth, n_chains=6, n_levels=3, chain_len=4, seed=9)

@@ -11,38 +11,10 @@ R_i = F(d_i)/F(d_{i-1}) - 1 are i.i.d. with 1 + R lognormal of mean 1:
     from the exact law of one clipped return (atoms at F and C, lognormal
     density between) convolved n-1 times on a fine grid.
 """
-import numpy as np
 import pytest
-from scipy.stats import norm
 
 import oracle as O
-from helpers import black_call
-
-
-def clipped_return_pmf(sigma, dt, fl, cl, n_cells):
-    """Law of max(min(R, cl), fl) on the grid fl + j (cl - fl)/n_cells: atoms
-    at both ends, each cell's mass split between its two end nodes."""
-    s = sigma * np.sqrt(dt)
-    x = np.linspace(fl, cl, n_cells + 1)
-    cdf = norm.cdf((np.log1p(x) + 0.5 * s * s) / s)  # P(R <= x)
-    pmf = np.zeros(n_cells + 1)
-    cell = np.diff(cdf)
-    pmf[:-1] += 0.5 * cell
-    pmf[1:] += 0.5 * cell
-    pmf[0] += cdf[0]
-    pmf[-1] += 1.0 - cdf[-1]
-    return x, pmf
-
-
-def exact_gbm_cliquet(sigma, T, n_resets, fl, cl, fg, cg, n_cells=4000):
-    dt = T / n_resets
-    x, pmf = clipped_return_pmf(sigma, dt, fl, cl, n_cells)
-    tot = pmf
-    for _ in range(n_resets - 2):
-        tot = np.convolve(tot, pmf)
-    k = n_resets - 1
-    grid = k * fl + (cl - fl) / n_cells * np.arange(tot.size)
-    return float(np.sum(tot * np.clip(grid, fg, cg)))
+from helpers import black_call, exact_gbm_cliquet
 
 
 def test_cliquet_without_global_limits_is_a_sum_of_call_spreads():
