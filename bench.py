@@ -31,14 +31,39 @@ sys.path.insert(0, ROOT)
 
 N_LEVELS, CHAIN_LEN, N_CHAINS, FACTOR = 200, 100, 4096, 0.95
 # Algorithmic work of one Hagan quote evaluation (eq. haganf + the misfit
-# term), by pipe: one power (exp2 of a precomputed log), one square root, one
-# logarithm, two divisions, and about 25 FP32 adds/multiplies.
-HAGAN_QUOTE_OPS = {"ex2": 1, "rsq": 1, "lg2": 1, "rcp": 2, "fp32": 25}
+# term), by pipe: (K f)^((1-beta)/2) and its reciprocal (two exp2 of a
+# precomputed log), one square root, one logarithm, two divisions, and about
+# 25 FP32 adds/multiplies.
+HAGAN_QUOTE_OPS = {"ex2": 2, "rsq": 1, "lg2": 1, "rcp": 2, "fp32": 25}
 # One log-Euler path-step: Box-Muller (log, sqrt, sin, cos), the exp of
 # nu-hat, ~12 FP32 operations, and half a Philox4x32-10 block (ten rounds of
 # two 32x32 multiplies, each a low and a high half: 20 integer multiplies).
 MC_STEP_OPS = {"lg2": 1, "rsq": 1, "sin": 2, "ex2": 1, "fp32": 12, "imad": 20}
 SMS = 152
+
+
+LEVEL_KERNEL_SOURCES = ["sa.cu", "engine.cuh", "sabr_math.cuh"]
+
+
+def profiled_traffic(profile, sources):
+    """DRAM bytes (read + write) per launch from a committed ncu summary under
+    profiles/, or None when the kernel's sources have changed since that
+    capture (the summary records their SHA-256)."""
+    import hashlib
+    import re
+    try:
+        text = open(os.path.join(ROOT, "profiles", profile)).read()
+    except OSError:
+        return None
+    t = re.search(r"^traffic_bytes_per_launch: (\d+)", text, re.M)
+    h = re.search(r"^source_sha256[^:]*: ([0-9a-f]{64})", text, re.M)
+    if not t or not h:
+        return None
+    d = hashlib.sha256()
+    for f in sources:
+        with open(os.path.join(ROOT, "paper_2407_20713_gb300", "csrc", f), "rb") as fh:
+            d.update(fh.read())
+    return int(t.group(1)) if d.hexdigest() == h.group(1) else None
 
 
 def pipe_bound(ops, rates, sm_mhz):
@@ -128,9 +153,10 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(smiles, market, n_levels=10):
+def cpu_baseline(smiles, market, n_levels=N_LEVELS):
     """The FP64 oracle, as it stands, on a bounded sample: smile 0 of the
-    surface, all 4096 chains, n_levels of the 200 levels (x 100 proposals)."""
+    surface, all 4096 chains, n_levels of the 200 levels (x 100 proposals);
+    by default one whole smile calibration (several seconds on 16 cores)."""
     import oracle as O
     sm, mkt = smiles[0], market[0]
     cores = os.cpu_count() or 1
@@ -160,13 +186,13 @@ def run_reference(args):
     vals, dts = [], []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        cb = cpu_baseline(smiles, market, n_levels=4)
+        cb = cpu_baseline(smiles, market, n_levels=40)
         dts.append(time.perf_counter() - t0)
         vals.append(cb["value"])
     value = float(np.mean(vals))
     cb["value"] = value
-    cb["sample"] = "each step: smile 1 of 10, %d chains, 4 of %d levels x %d proposals" % (N_CHAINS, N_LEVELS,
-                                                                                           CHAIN_LEN)
+    cb["sample"] = "each step: smile 1 of 10, %d chains, 40 of %d levels x %d proposals" % (N_CHAINS, N_LEVELS,
+                                                                                            CHAIN_LEN)
     line = {"impl": "reference", "metric": "SABR SA cost evals/s (static Hagan surface, 10x21, FP32 bulk)",
             "value": value, "unit": "cost-evals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * float(np.mean(dts)), "higher_is_better": True, "scaling": "weak",
@@ -218,6 +244,81 @@ def measure_mc(sg, torch, stream, rates, sm_mhz):
         res["roofline"] = {"bound": "alu", "pipe": pipe, "ops_per_path_step": MC_STEP_OPS,
                            "achieved": res["value"], "peak": peak, "unit": "path-steps/s",
                            "frac": res["value"] / peak}
+    return res
+
+
+def measure_cliquet(sg, torch, stream, rates, sm_mhz):
+    """sabr_mc_cliquet on the Sec. 6.3 contract (one year, 4 resets, local
+    limits -2%/+2%, global floor 0 and cap 0.2), 2^20 paths, 250 steps a
+    year, DSabr_I dynamics with synthetic EUR/USD-like parameters."""
+    n_paths, spy = 1 << 20, 250.0
+    p = [0.11, 0.75, -0.25, 0.6, 0.9, 1.4]
+    steps = grid_steps(np.array([0.25, 0.5, 0.75, 1.0]), spy)
+    out = {}
+    for prec, name in ((sg.FP32, "fp32"), (sg.FP64, "fp64")):
+        sg.mc_cliquet(sg.DYN_I, p, 1.0, 1.0, 4, -0.02, 0.02, 0.0, 0.2, n_paths=1 << 14, steps_per_year=spy,
+                      prec=prec)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pr, se = sg.mc_cliquet(sg.DYN_I, p, 1.0, 1.0, 4, -0.02, 0.02, 0.0, 0.2, n_paths=n_paths,
+                               steps_per_year=spy, seed=11, prec=prec)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        out[name] = {"ms": ms, "value": n_paths * steps / (ms / 1e3), "unit": "path-steps/s",
+                     "price": float(pr.item()), "stderr": float(se.item())}
+    res = {"workload": "cliquet T=1y, 4 resets, 2^20 paths, %d steps, DSabr_I" % steps,
+           "value": out["fp32"]["value"], "unit": "path-steps/s", "ms": out["fp32"]["ms"], "fp64_form": out["fp64"],
+           "price": out["fp32"]["price"]}
+    if rates:
+        peak, pipe, _ = pipe_bound(MC_STEP_OPS, rates, sm_mhz)
+        res["roofline"] = {"bound": "alu", "pipe": pipe, "ops_per_path_step": MC_STEP_OPS,
+                           "achieved": res["value"], "peak": peak, "unit": "path-steps/s",
+                           "frac": res["value"] / peak}
+    return res
+
+
+def measure_mc_calibration(sg, torch, stream, rates, sm_mhz):
+    """Technique II (SA with the Monte Carlo price misfit) on the MC surface:
+    8 maturities x 15 calls, 256 chains, 2^16 paths x 250 steps a year per
+    cost evaluation (504 grid steps), FP32 paths; a sample of the schedule
+    (2 levels x 5 proposals in FP32, 1 level x 2 proposals in FP64), as the
+    full 200 x 100 schedule takes minutes."""
+    from paper_2407_20713_gb300 import workloads
+    w = workloads.mc_surface()
+    m = w.meta
+    mkt = sg.mc_price(sg.HAGAN, w.truth, 1.0, w.T, w.K, n_paths=m["market_paths"], steps_per_year=250,
+                      seed=m["market_seed"])[0].cpu().numpy()
+    steps = grid_steps(w.T, m["steps_per_year"])
+    out = {}
+    for prec, name, levels, clen in ((sg.FP32, "fp32", 2, 5), (sg.FP64, "fp64", 1, 2)):
+        pb = sg.CalibrationProblem(model=sg.HAGAN, T=w.T, K=w.K, market=mkt, lo=w.lo, hi=w.hi, prec=prec,
+                                   cost=sg.COST_MC_PRICE, n_chains=w.n_chains, n_levels=levels, chain_len=clen,
+                                   mc_paths=m["cal_paths"], mc_steps_per_year=m["steps_per_year"],
+                                   mc_seed=m["cal_seed"], seed=5)
+        plan = sg.Plan([pb], use_graph=True)
+        plan.run(stream)
+        plan.results()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan.run(stream)
+        b.record(stream)
+        r = plan.results()[0]
+        ms = a.elapsed_time(b)
+        plan.close()
+        # the init evaluation of x0 is one more MC pricing per problem
+        evals = r.n_evals + 1
+        out[name] = {"value": evals / (ms / 1e3), "unit": "cost-evals/s", "ms": ms, "levels": levels,
+                     "chain_len": clen, "path_steps_per_s": evals * m["cal_paths"] * steps / (ms / 1e3)}
+    res = {"workload": "Technique II, static Hagan, 8 x 15 calls, 256 chains, 2^16 paths x %d steps per cost "
+                       "evaluation" % steps,
+           "value": out["fp32"]["value"], "unit": "cost-evals/s", "path_steps_per_s": out["fp32"]["path_steps_per_s"],
+           "sample": "2 of 200 levels x 5 of 100 proposals (FP32); 1 level x 2 proposals (FP64)",
+           "fp64_form": out["fp64"]}
+    if rates:
+        peak, pipe, _ = pipe_bound(MC_STEP_OPS, rates, sm_mhz)
+        res["roofline"] = {"bound": "alu", "pipe": pipe, "unit": "path-steps/s", "peak": peak,
+                           "achieved": res["path_steps_per_s"], "frac": res["path_steps_per_s"] / peak}
     return res
 
 
@@ -457,10 +558,11 @@ def run_ours(args):
         peak_note = ("measured pipe rates (sabr_probe_pipe_rates) x 152 SMs x median SM clock; binding pipe: %s"
                      % pipe)
     else:
-        peak = SMS * sm_mhz * 1e6 / (1 / 32 + 4 / 16) / 1e9
+        peak = SMS * sm_mhz * 1e6 / (2 / 32 + 4 / 16) / 1e9
         peak_note = "nominal SFU rates (ex2 32, others 16 per SM clock) x 152 SMs x median SM clock"
     roofline = {"bound": "alu", "kernel": "sa_level_kernel<float,HAGAN>", "achieved": achieved, "peak": peak,
-                "unit": "Gquote-eval/s", "frac": achieved / peak, "traffic": None,
+                "unit": "Gquote-eval/s", "frac": achieved / peak,
+                "traffic": profiled_traffic("sa_level_kernel_hagan_static_surface.md", LEVEL_KERNEL_SOURCES),
                 "launch_ms": lvl_ms, "quote_evals_per_launch": quote_evals_per_launch, "peak_from": peak_note,
                 "pipe_rates_per_sm_clk": rates}
 
@@ -499,6 +601,8 @@ def run_ours(args):
 
     if rank == 0 and not args.no_extra and args.case == "full":
         for key, fn in (("mc", lambda: measure_mc(sg, torch, stream, rates, sm_mhz)),
+                        ("mc_calibration", lambda: measure_mc_calibration(sg, torch, stream, rates, sm_mhz)),
+                        ("cliquet", lambda: measure_cliquet(sg, torch, stream, rates, sm_mhz)),
                         ("dynamic", lambda: measure_dynamic(sg, torch, stream)),
                         ("serving", lambda: measure_serving_loads(sg, args.serve_requests))):
             try:
