@@ -37,38 +37,60 @@ __global__ void __launch_bounds__(kClqBlock) cliquet_kernel(McDev P, const doubl
   const R log_abs = (R)(P.log_absorb * PathUnits<R>::kLogUnit);
   const R fl = (R)floor_l, cl = (R)cap_l;
   double s1 = 0.0, s2 = 0.0;
+  // two paths per thread (path, path + stride) advance together
+  constexpr int NPT = kMcPathsPerThread;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t path = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; path < P.n_paths; path += stride) {
-    PathState<R> st{lnf, lna, false};
-    R prev = (R)0, sum = (R)0;
+  for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p0 < P.n_paths; p0 += NPT * stride) {
+    int64_t path[NPT];
+    PathState<R> st[NPT];
+    R prev[NPT], sum[NPT];
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+      path[k] = p0 + k * stride;
+      st[k] = PathState<R>{lnf, lna, false};
+      prev[k] = (R)0;
+      sum[k] = (R)0;
+    }
     int reset = 0, i_land = land[0];
     auto at_reset = [&]() {
-      const R F = st.absorbed ? (R)0 : PathUnits<R>::expu(st.lnF);
-      if (reset >= 1) {
-        // R_i = F(d_i)/F(d_{i-1}) - 1; a path absorbed before d_{i-1}
-        // adds R_i = 0 (0 to 0)
-        const R ret = prev > (R)0 ? F / prev - (R)1 : (R)0;
-        const R c = ret < cl ? ret : cl;
-        sum += c > fl ? c : fl;
+#pragma unroll
+      for (int k = 0; k < NPT; ++k) {
+        const R F = st[k].absorbed ? (R)0 : PathUnits<R>::expu(st[k].lnF);
+        if (reset >= 1) {
+          // R_i = F(d_i)/F(d_{i-1}) - 1; a path absorbed before d_{i-1}
+          // adds R_i = 0 (0 to 0)
+          const R ret = prev[k] > (R)0 ? F / prev[k] - (R)1 : (R)0;
+          const R c = ret < cl ? ret : cl;
+          sum[k] += c > fl ? c : fl;
+        }
+        prev[k] = F;
       }
-      prev = F;
       ++reset;
       i_land = reset < P.n_mats ? land[reset] : -1;
     };
     for (int i = 0; i < P.n_steps; i += 2) {
-      const uint4 w = path_words(P, path, i);
-      path_step<R>(tab[i], w.x, w.y, beta_m1, log_abs, st);
+      uint4 w[NPT];
+#pragma unroll
+      for (int k = 0; k < NPT; ++k) w[k] = path_words(P, path[k], i);
+#pragma unroll
+      for (int k = 0; k < NPT; ++k) path_step<R>(tab[i], w[k].x, w[k].y, beta_m1, log_abs, st[k]);
       if (i == i_land) at_reset();
       if (i + 1 < P.n_steps) {
-        path_step<R>(tab[i + 1], w.z, w.w, beta_m1, log_abs, st);
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) path_step<R>(tab[i + 1], w[k].z, w[k].w, beta_m1, log_abs, st[k]);
         if (i + 1 == i_land) at_reset();
       }
     }
-    double g = (double)sum;
-    g = g < cap_g ? g : cap_g;
-    g = g > floor_g ? g : floor_g;
-    s1 += g;
-    s2 += g * g;
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+      if (path[k] < P.n_paths) {
+        double g = (double)sum[k];
+        g = g < cap_g ? g : cap_g;
+        g = g > floor_g ? g : floor_g;
+        s1 += g;
+        s2 += g * g;
+      }
+    }
   }
   red[0][threadIdx.x] = s1;
   red[1][threadIdx.x] = s2;
@@ -147,7 +169,19 @@ extern "C" sabr_status sabr_mc_cliquet(sabr_model model, const double* params, d
   const size_t smem = (size_t)h.n_steps * (prec == SABR_FP64 ? sizeof(StepCoef<double>) : sizeof(StepCoef<float>)) +
                       (size_t)n_resets * sizeof(int);
   if (smem > 200 * 1024) return fail(SABR_EINVAL, "too many time steps for one launch");
-  const int blocks = (int)std::min<int64_t>(152 * 8, (n_paths + kClqBlock - 1) / kClqBlock);
+  // resident blocks of the GPU (grid-stride; no partly filled second wave),
+  // and no more than the paths need at two paths per thread
+  int per_sm = 8;
+  if (prec == SABR_FP64) {
+    cudaFuncSetAttribute(cliquet_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cliquet_kernel<double>, kClqBlock, smem);
+  } else {
+    cudaFuncSetAttribute(cliquet_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cliquet_kernel<float>, kClqBlock, smem);
+  }
+  per_sm = std::min(std::max(per_sm, 1), 8);
+  const int64_t per_block = (int64_t)kClqBlock * kMcPathsPerThread;
+  const int blocks = (int)std::min<int64_t>(152 * (int64_t)per_sm, (n_paths + per_block - 1) / per_block);
   const size_t img = mc_image_bytes(h);
   const size_t params_off = (img + 255) & ~(size_t)255;
   const size_t part_off = params_off + 256;
