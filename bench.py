@@ -86,9 +86,10 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 form")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extra", action="store_true", help="skip the MC, dynamic and serving measurements")
-    ap.add_argument("--case", choices=["full", "small", "mc"], default="full",
+    ap.add_argument("--case", choices=["full", "small", "mc", "cliquet"], default="full",
                     help="small: 2 smiles x 10 levels, main measurement only; mc: one 2^20-path MC pricing "
-                         "of the MC surface (both for profiler captures)")
+                         "of the MC surface; cliquet: one 2^20-path cliquet (the last three for profiler "
+                         "captures)")
     ap.add_argument("--serve-requests", type=int, default=400)
     return ap.parse_args()
 
@@ -278,23 +279,71 @@ def measure_cliquet(sg, torch, stream, rates, sm_mhz):
     return res
 
 
+def measure_single_smile(sg, torch, stream):
+    """cfg 1: one Hagan smile (T = 1, 15 strikes), 64 chains, 200 levels x 100
+    proposals: the time of one whole calibration in FP64 and in FP32 on the
+    GPU, and of the oracle (FP64, all host cores) on the same problem."""
+    import oracle as O
+    from paper_2407_20713_gb300 import workloads
+    w = workloads.one_smile()
+    mkt = O.implied_vol(O.HAGAN, w.truth, 1.0, w.T, w.K) + w.noise
+    out = {}
+    for prec, name in ((sg.FP64, "fp64"), (sg.FP32, "fp32")):
+        pb = sg.CalibrationProblem(model=sg.HAGAN, T=w.T, K=w.K, market=mkt, lo=w.lo, hi=w.hi, prec=prec,
+                                   n_chains=w.n_chains, n_levels=N_LEVELS, chain_len=CHAIN_LEN, factor=FACTOR,
+                                   seed=1)
+        plan = sg.Plan([pb], use_graph=True)
+        for _ in range(3):
+            plan.run(stream)
+            plan.results()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan.run(stream)
+        b.record(stream)
+        r = plan.results()[0]
+        ms = a.elapsed_time(b)
+        plan.close()
+        out[name] = {"ms_per_calibration": ms, "cost_evals_per_s": r.n_evals / (ms / 1e3),
+                     "misfit_fp64": r.misfit_fp64}
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    o = O.sa_calibrate(O.HAGAN, 1.0, w.T, w.K, mkt, w.lo, w.hi, n_chains=w.n_chains, factor=FACTOR,
+                       n_levels=N_LEVELS, chain_len=CHAIN_LEN, seed=1, n_threads=cores)
+    dt = time.perf_counter() - t0
+    out["oracle"] = {"ms_per_calibration": 1e3 * dt, "cores": cores, "misfit": o["misfit"]}
+    out["workload"] = "one Hagan smile, T = 1, 15 strikes, 64 chains, 200 levels x 100 proposals"
+    return out
+
+
+def _case2_ok(x, tmax, n=2001):
+    """rho(t) in [-1, 1] and nu(t) > 0 on [0, tmax] for Case II parameters
+    (dense grid; host-side check of a synthetic truth)."""
+    t = np.linspace(0.0, tmax, n)
+    rho = (x[2] + x[8] * t) * np.exp(-x[4] * t) + x[6]
+    nu = (x[3] + x[9] * t) * np.exp(-x[5] * t) + x[7]
+    return bool(np.all(np.abs(rho) <= 0.999) and np.all(nu > 1e-3))
+
+
 def measure_mc_calibration(sg, torch, stream, rates, sm_mhz):
     """Technique II (SA with the Monte Carlo price misfit) on the MC surface:
     8 maturities x 15 calls, 256 chains, 2^16 paths x 250 steps a year per
-    cost evaluation (504 grid steps), FP32 paths; a sample of the schedule
-    (2 levels x 5 proposals in FP32, 1 level x 2 proposals in FP64), as the
-    full 200 x 100 schedule takes minutes."""
+    cost evaluation (504 grid steps), FP32 paths.  Static Hagan (cfg 4): a
+    sample of 20 levels x 10 proposals of the 200 x 100 schedule in FP32,
+    1 level x 2 proposals in FP64.  DSabr_II (the paper's Technique II
+    model): 2 levels x 5 proposals in FP32."""
     from paper_2407_20713_gb300 import workloads
     w = workloads.mc_surface()
     m = w.meta
-    mkt = sg.mc_price(sg.HAGAN, w.truth, 1.0, w.T, w.K, n_paths=m["market_paths"], steps_per_year=250,
-                      seed=m["market_seed"])[0].cpu().numpy()
     steps = grid_steps(w.T, m["steps_per_year"])
-    out = {}
-    for prec, name, levels, clen in ((sg.FP32, "fp32", 2, 5), (sg.FP64, "fp64", 1, 2)):
-        pb = sg.CalibrationProblem(model=sg.HAGAN, T=w.T, K=w.K, market=mkt, lo=w.lo, hi=w.hi, prec=prec,
-                                   cost=sg.COST_MC_PRICE, n_chains=w.n_chains, n_levels=levels, chain_len=clen,
-                                   mc_paths=m["cal_paths"], mc_steps_per_year=m["steps_per_year"],
+    dyn = workloads.dynamic_surface(case=2, feasible=lambda x: _case2_ok(x, float(w.T.max())))
+
+    def run(model, truth, lo, hi, prec, levels, clen):
+        mkt = sg.mc_price(model, truth, 1.0, w.T, w.K, n_paths=m["market_paths"], steps_per_year=250,
+                          seed=m["market_seed"])[0].cpu().numpy()
+        keep = mkt >= 1e-6  # quotes priced below 1e-6 f are left out
+        pb = sg.CalibrationProblem(model=model, T=w.T[keep], K=w.K[keep], market=mkt[keep], lo=lo, hi=hi,
+                                   prec=prec, cost=sg.COST_MC_PRICE, n_chains=w.n_chains, n_levels=levels,
+                                   chain_len=clen, mc_paths=m["cal_paths"], mc_steps_per_year=m["steps_per_year"],
                                    mc_seed=m["cal_seed"], seed=5)
         plan = sg.Plan([pb], use_graph=True)
         plan.run(stream)
@@ -306,15 +355,20 @@ def measure_mc_calibration(sg, torch, stream, rates, sm_mhz):
         r = plan.results()[0]
         ms = a.elapsed_time(b)
         plan.close()
-        # the init evaluation of x0 is one more MC pricing per problem
-        evals = r.n_evals + 1
-        out[name] = {"value": evals / (ms / 1e3), "unit": "cost-evals/s", "ms": ms, "levels": levels,
-                     "chain_len": clen, "path_steps_per_s": evals * m["cal_paths"] * steps / (ms / 1e3)}
+        evals = r.n_evals + 1  # the init evaluation of x0 is one more MC pricing
+        return {"value": evals / (ms / 1e3), "unit": "cost-evals/s", "ms": ms, "levels": levels,
+                "chain_len": clen, "quotes": int(keep.sum()),
+                "path_steps_per_s": evals * m["cal_paths"] * steps / (ms / 1e3)}
+
+    hag32 = run(sg.HAGAN, w.truth, w.lo, w.hi, sg.FP32, 20, 10)
+    hag64 = run(sg.HAGAN, w.truth, w.lo, w.hi, sg.FP64, 1, 2)
+    dyn32 = run(sg.DYN_II, dyn.truth, dyn.lo, dyn.hi, sg.FP32, 2, 5)
     res = {"workload": "Technique II, static Hagan, 8 x 15 calls, 256 chains, 2^16 paths x %d steps per cost "
                        "evaluation" % steps,
-           "value": out["fp32"]["value"], "unit": "cost-evals/s", "path_steps_per_s": out["fp32"]["path_steps_per_s"],
-           "sample": "2 of 200 levels x 5 of 100 proposals (FP32); 1 level x 2 proposals (FP64)",
-           "fp64_form": out["fp64"]}
+           "value": hag32["value"], "unit": "cost-evals/s", "path_steps_per_s": hag32["path_steps_per_s"],
+           "ms": hag32["ms"], "sample": "20 of 200 levels x 10 of 100 proposals (FP32); 1 level x 2 proposals "
+                                       "(FP64)",
+           "fp64_form": hag64, "dsabr2_fp32": dict(dyn32, sample="2 levels x 5 proposals")}
     if rates:
         peak, pipe, _ = pipe_bound(MC_STEP_OPS, rates, sm_mhz)
         res["roofline"] = {"bound": "alu", "pipe": pipe, "unit": "path-steps/s", "peak": peak,
@@ -415,11 +469,13 @@ def measure_serving(sg, n_requests, rate_hz):
             "steps": st["steps"], "kernel_launches": st["kernel_launches"], "wall_s": wall}
 
 def measure_serving_loads(sg, n_requests):
-    """Capacity (all requests at once), then Poisson arrivals at 80% of it;
-    beside it the plain FP64 one-request-per-launch form on a sample."""
+    """Capacity (all requests at once), then Poisson arrivals at 50%, 80% and
+    95% of it (half the requests each); beside it the plain FP64
+    one-request-per-launch form on a sample."""
     burst = measure_serving(sg, n_requests, rate_hz=1e9)
     cap = burst["calibrations_per_s"]
-    at80 = measure_serving(sg, n_requests, rate_hz=0.8 * cap)
+    loads = {"load%d" % int(100 * f): measure_serving(sg, max(1, n_requests // 2), rate_hz=f * cap)
+             for f in (0.5, 0.8, 0.95)}
     from paper_2407_20713_gb300 import workloads
     sample = workloads.serving_stream(n=24, rate_hz=1.0)
     t0 = time.perf_counter()
@@ -434,8 +490,10 @@ def measure_serving_loads(sg, n_requests):
                                            chain_len=q.chain_len, seed=11))
         n += 1
     fp64_rate = n / (time.perf_counter() - t0)
-    return {"capacity": burst, "load80": at80,
-            "fp64_one_request_per_launch": {"calibrations_per_s": fp64_rate, "sample": "%d formula requests" % n}}
+    out = {"capacity": burst}
+    out.update(loads)
+    out["fp64_one_request_per_launch"] = {"calibrations_per_s": fp64_rate, "sample": "%d formula requests" % n}
+    return out
 
 
 def run_mc_case():
@@ -450,6 +508,19 @@ def run_mc_case():
         sg.mc_price(sg.HAGAN, w.truth, 1.0, w.T, w.K, n_paths=1 << 20, steps_per_year=250, seed=1, prec=prec)
     torch.cuda.synchronize()
     print(json.dumps({"case": "mc", "ok": True}))
+
+
+def run_cliquet_case():
+    """One sabr_mc_cliquet of the Sec. 6.3 contract at 2^20 paths (profiling)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2407_20713_gb300 as sg
+    p = [0.11, 0.75, -0.25, 0.6, 0.9, 1.4]
+    for _ in range(2):
+        sg.mc_cliquet(sg.DYN_I, p, 1.0, 1.0, 4, -0.02, 0.02, 0.0, 0.2, n_paths=1 << 20, steps_per_year=250)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "cliquet", "ok": True}))
 
 
 def aggregate(t_local, units_local, e2e_local, dist=None):
@@ -601,6 +672,7 @@ def run_ours(args):
 
     if rank == 0 and not args.no_extra and args.case == "full":
         for key, fn in (("mc", lambda: measure_mc(sg, torch, stream, rates, sm_mhz)),
+                        ("single_smile", lambda: measure_single_smile(sg, torch, stream)),
                         ("mc_calibration", lambda: measure_mc_calibration(sg, torch, stream, rates, sm_mhz)),
                         ("cliquet", lambda: measure_cliquet(sg, torch, stream, rates, sm_mhz)),
                         ("dynamic", lambda: measure_dynamic(sg, torch, stream)),
@@ -624,5 +696,7 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.case == "mc":
         run_mc_case()
+    elif a.case == "cliquet":
+        run_cliquet_case()
     else:
         run_ours(a)
