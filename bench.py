@@ -170,6 +170,22 @@ def cpu_baseline(smiles, market, n_levels=N_LEVELS):
                       % (sm.n_chains, n_levels, N_LEVELS, CHAIN_LEN, dt)}
 
 
+def cpu_baseline_single_smile():
+    """The oracle (FP64, all host cores) on one whole cfg 1 calibration: one
+    Hagan smile, 15 strikes, 64 chains, 200 levels x 100 proposals."""
+    import oracle as O
+    from paper_2407_20713_gb300 import workloads
+    w = workloads.one_smile()
+    mkt = O.implied_vol(O.HAGAN, w.truth, 1.0, w.T, w.K) + w.noise
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    o = O.sa_calibrate(O.HAGAN, 1.0, w.T, w.K, mkt, w.lo, w.hi, n_chains=w.n_chains, factor=FACTOR,
+                       n_levels=N_LEVELS, chain_len=CHAIN_LEN, seed=1, n_threads=cores)
+    dt = time.perf_counter() - t0
+    return {"ms_per_calibration": 1e3 * dt, "cores": cores, "misfit": o["misfit"],
+            "workload": "one Hagan smile, T = 1, 15 strikes, 64 chains, 200 levels x 100 proposals"}
+
+
 def oracle_market(smiles):
     import oracle as O
     return [O.implied_vol(O.HAGAN, sm.truth, 1.0, sm.T, sm.K) + sm.noise for sm in smiles]
@@ -282,11 +298,10 @@ def measure_cliquet(sg, torch, stream, rates, sm_mhz):
 def measure_single_smile(sg, torch, stream):
     """cfg 1: one Hagan smile (T = 1, 15 strikes), 64 chains, 200 levels x 100
     proposals: the time of one whole calibration in FP64 and in FP32 on the
-    GPU, and of the oracle (FP64, all host cores) on the same problem."""
-    import oracle as O
+    GPU (the oracle's time on it is part of the CPU baseline)."""
     from paper_2407_20713_gb300 import workloads
     w = workloads.one_smile()
-    mkt = O.implied_vol(O.HAGAN, w.truth, 1.0, w.T, w.K) + w.noise
+    mkt = sg.implied_vol(sg.HAGAN, w.truth, 1.0, w.T, w.K, prec=sg.FP64).cpu().numpy() + w.noise
     out = {}
     for prec, name in ((sg.FP64, "fp64"), (sg.FP32, "fp32")):
         pb = sg.CalibrationProblem(model=sg.HAGAN, T=w.T, K=w.K, market=mkt, lo=w.lo, hi=w.hi, prec=prec,
@@ -305,12 +320,6 @@ def measure_single_smile(sg, torch, stream):
         plan.close()
         out[name] = {"ms_per_calibration": ms, "cost_evals_per_s": r.n_evals / (ms / 1e3),
                      "misfit_fp64": r.misfit_fp64}
-    cores = os.cpu_count() or 1
-    t0 = time.perf_counter()
-    o = O.sa_calibrate(O.HAGAN, 1.0, w.T, w.K, mkt, w.lo, w.hi, n_chains=w.n_chains, factor=FACTOR,
-                       n_levels=N_LEVELS, chain_len=CHAIN_LEN, seed=1, n_threads=cores)
-    dt = time.perf_counter() - t0
-    out["oracle"] = {"ms_per_calibration": 1e3 * dt, "cores": cores, "misfit": o["misfit"]}
     out["workload"] = "one Hagan smile, T = 1, 15 strikes, 64 chains, 200 levels x 100 proposals"
     return out
 
@@ -379,11 +388,10 @@ def measure_mc_calibration(sg, torch, stream, rates, sm_mhz):
 def measure_dynamic(sg, torch, stream, levels=10):
     """Joint dynamic fits on 12 maturities x 21 strikes, 8192 chains each, one
     Case I and one Case II surface, FP32; `levels` of the 200 levels."""
-    import oracle  # noqa: F401  (not used: market vols come from the library)
     from paper_2407_20713_gb300 import workloads
     res = {}
     for case, model in ((1, sg.DYN_I), (2, sg.DYN_II)):
-        w = workloads.dynamic_surface(case=case)
+        w = workloads.dynamic_surface(case=case, feasible=lambda x: _case2_ok(x, float(workloads.DYN_MATURITIES[-1])))
         mkt = sg.implied_vol(model, w.truth, 1.0, w.T, w.K, prec=sg.FP64).cpu().numpy() + w.noise
         pb = sg.CalibrationProblem(model=model, T=w.T, K=w.K, market=mkt, lo=w.lo, hi=w.hi, prec=sg.FP32,
                                    n_chains=w.n_chains, n_levels=levels, chain_len=CHAIN_LEN, seed=3)
@@ -683,6 +691,7 @@ def run_ours(args):
                 line[key] = {"error": repr(exc)}
     if rank == 0 and not args.no_cpu and args.case == "full":
         line["cpu_baseline"] = cpu_baseline(smiles, market)
+        line["cpu_baseline"]["single_smile"] = cpu_baseline_single_smile()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

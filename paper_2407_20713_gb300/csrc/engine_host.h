@@ -43,7 +43,8 @@ void launch_level(int prec, int model, const ProblemDev* probs, const int4* bmap
 void launch_persistent(int prec, int model, const ProblemDev* probs, const int4* work, const int* n_work, int grid,
                        size_t smem, cudaStream_t s);
 void launch_finalize(int prec, int model, const ProblemDev* probs, const int* plist, int n, cudaStream_t s);
-// Resident 256-thread blocks per SM of the persistent kernel at `smem`.
+// Resident 256-thread blocks per SM of the level kernel at `smem` (the
+// server's grid-stride launches).
 int persistent_blocks_per_sm(int prec, int model, size_t smem);
 
 }  // namespace sabr

@@ -502,7 +502,8 @@ static int next_pow2(int v) {
 
 // About 24 quotes per lane (a lane runs its quote loop four quotes at a
 // time), widened while the batch has fewer than 152 x 256 threads and quotes
-// remain to split; the dynamic models take at least one lane per maturity.
+// remain to split; the dynamic models take one lane per maturity (Case I)
+// or per two maturities (Case II).
 int choose_lanes(int n_quotes, int n_mats, int model, long long batch_chains) {
   if (const char* e = std::getenv("SABR_LANES")) {
     int g = std::atoi(e);
@@ -511,7 +512,11 @@ int choose_lanes(int n_quotes, int n_mats, int model, long long batch_chains) {
   // fewer lanes repeat the per-proposal work (Philox, proposal,
   // Metropolis, lane sum) less often
   int G = next_pow2((n_quotes + 23) / 24);
-  if (model == SABR_DYN_I || model == SABR_DYN_II) G = std::max(G, next_pow2(n_mats));
+  // Case I: one lane per maturity for its closed forms; Case II: the lanes
+  // share each maturity's eta2^2 quadrature, and a lane takes up to two
+  // maturities' closed-form parts
+  if (model == SABR_DYN_I) G = std::max(G, next_pow2(n_mats));
+  if (model == SABR_DYN_II) G = std::max(G, std::max(1, next_pow2(n_mats) / 2));
   G = std::min(G, 32);
   const int cap = std::min(32, next_pow2(n_quotes));
   while (G < cap && batch_chains * G < 152 * 256) G <<= 1;

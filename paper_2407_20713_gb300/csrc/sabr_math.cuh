@@ -136,8 +136,10 @@ constexpr uint32_t kTagSA = 0x53410000u;
 constexpr uint32_t kTagMC = 0x4D430000u;
 
 // 23 random bits + 1/2, scaled by 2^-23: exact in float, strictly in (0,1).
+// Written as one fused multiply-add, (w >> 9) 2^-23 + 2^-24, whose product
+// and sum are both exact, so the value is the same.
 template <class R> __device__ __forceinline__ R u01(uint32_t w) {
-  return ((R)(w >> 9) + (R)0.5) * (R)1.1920928955078125e-07;
+  return fma((R)(w >> 9), (R)1.1920928955078125e-07, (R)5.9604644775390625e-08);
 }
 
 // ---------------------------------------------------------------------------
@@ -406,15 +408,15 @@ __device__ __forceinline__ void case1_coeffs(R nu0, R rho0, R a, R b, R T, R out
 // is used (for m <= 4 in FP32 emulation against quadrature: relative error
 // at most 1.6e-6 with 12 series terms below 2).
 // ---------------------------------------------------------------------------
+// phi_0..phi_M at x >= 0, given e = e^{-x}.
 template <class R, int M>
-__device__ __forceinline__ void phi_vec(R x, R* phi) {
-  const R e = m_exp(-x);
+__device__ __forceinline__ void phi_vec_e(R x, R e, R* phi) {
   if (x < (R)Tr<R>::kSeriesMax) {
     constexpr int N = Tr<R>::kSeries;
-    R s = (R)1;
+    // S_M(x) = sum_{n=0..N} x^n/(M+n+1)! by Horner's rule, one FMA a term
+    R S = (R)(1.0 / cx_fact(M + N + 1));
 #pragma unroll
-    for (int n = N; n >= 1; --n) s = (R)1 + s * x * (R)(1.0 / (M + 1 + n));
-    R S = s * (R)(1.0 / cx_fact(M + 1));
+    for (int n = N - 1; n >= 0; --n) S = S * x + (R)(1.0 / cx_fact(M + n + 1));
     phi[M] = (R)cx_fact(M) * e * S;
 #pragma unroll
     for (int m = M - 1; m >= 0; --m) {
@@ -427,6 +429,11 @@ __device__ __forceinline__ void phi_vec(R x, R* phi) {
 #pragma unroll
     for (int m = 1; m <= M; ++m) phi[m] = ((R)m * phi[m - 1] - e) * ix;
   }
+}
+
+template <class R, int M>
+__device__ __forceinline__ void phi_vec(R x, R* phi) {
+  phi_vec_e<R, M>(x, m_exp(-x), phi);
 }
 
 // nu1^2 = 3 int_0^1 (1-tau)^2 nu^2,  nu2^2 = 6 int_0^1 (1-tau) tau nu^2,
@@ -473,9 +480,10 @@ __device__ __forceinline__ void case2_single(R rho0, R nu0, R A, R B, R dr, R dn
 template <class R>
 __device__ __forceinline__ R case2_G(R s, R rho0, R nu0, R A, R B, R dr, R dn, R Qr, R Qn) {
   R pAB[3], pB[2], pA[2];
-  phi_vec<R, 2>((A + B) * s, pAB);
-  phi_vec<R, 1>(B * s, pB);
-  phi_vec<R, 1>(A * s, pA);
+  const R eA = m_exp(-A * s), eB = m_exp(-B * s);  // e^{-(A+B)s} = eA eB
+  phi_vec_e<R, 2>((A + B) * s, eA * eB, pAB);
+  phi_vec_e<R, 1>(B * s, eB, pB);
+  phi_vec_e<R, 1>(A * s, eA, pA);
   const R k0 = nu0 * rho0, k1 = nu0 * Qr + Qn * rho0, k2 = Qn * Qr;
   const R s2 = s * s;
   return s * (k0 * pAB[0] + s * k1 * pAB[1] + s2 * k2 * pAB[2]) +
