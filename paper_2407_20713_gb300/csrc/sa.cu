@@ -512,11 +512,11 @@ int choose_lanes(int n_quotes, int n_mats, int model, long long batch_chains) {
   // fewer lanes repeat the per-proposal work (Philox, proposal,
   // Metropolis, lane sum) less often
   int G = next_pow2((n_quotes + 23) / 24);
-  // Case I: one lane per maturity for its closed forms; Case II: the lanes
-  // share each maturity's eta2^2 quadrature, and a lane takes up to two
-  // maturities' closed-form parts
+  // Case I: one lane per maturity for its closed forms.  Case II: the
+  // per-maturity functions dominate (the lanes share each maturity's eta2^2
+  // quadrature), so one lane per two maturities whatever the quote count
   if (model == SABR_DYN_I) G = std::max(G, next_pow2(n_mats));
-  if (model == SABR_DYN_II) G = std::max(G, std::max(1, next_pow2(n_mats) / 2));
+  if (model == SABR_DYN_II) G = std::max(1, next_pow2(n_mats) / 2);
   G = std::min(G, 32);
   const int cap = std::min(32, next_pow2(n_quotes));
   while (G < cap && batch_chains * G < 152 * 256) G <<= 1;

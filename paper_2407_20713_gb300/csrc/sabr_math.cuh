@@ -21,7 +21,7 @@ template <> struct Tr<float> {
   static constexpr int kSeries = 12;          // phi_m series terms below kSeriesMax
   static constexpr double kSeriesMax = 2.0;   // (the recurrence above it)
   static constexpr int kCase1Series = 20;     // Case I series terms (argument < 2)
-  static constexpr int kGauss = 8;            // Gauss-Legendre nodes per panel
+  static constexpr int kGauss = 6;            // Gauss-Legendre nodes per panel
 };
 template <> struct Tr<double> {
   static constexpr int kSeries = 32;
