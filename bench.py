@@ -260,7 +260,11 @@ def measure_mc(sg, torch, stream, rates, sm_mhz):
         peak, pipe, _ = pipe_bound(MC_STEP_OPS, rates, sm_mhz)
         res["roofline"] = {"bound": "alu", "pipe": pipe, "ops_per_path_step": MC_STEP_OPS,
                            "achieved": res["value"], "peak": peak, "unit": "path-steps/s",
-                           "frac": res["value"] / peak}
+                           "frac": res["value"] / peak,
+                           "traffic": profiled_traffic("mc_paths_kernel_mc_surface.md",
+                                                       ["mc.cu", "mc.cuh", "sabr_math.cuh"]),
+                           "traffic_note": "DRAM bytes per launch from the 2^20-path capture: the tables, "
+                                           "independent of the path count"}
     return res
 
 
@@ -291,7 +295,9 @@ def measure_cliquet(sg, torch, stream, rates, sm_mhz):
         peak, pipe, _ = pipe_bound(MC_STEP_OPS, rates, sm_mhz)
         res["roofline"] = {"bound": "alu", "pipe": pipe, "ops_per_path_step": MC_STEP_OPS,
                            "achieved": res["value"], "peak": peak, "unit": "path-steps/s",
-                           "frac": res["value"] / peak}
+                           "frac": res["value"] / peak,
+                           "traffic": profiled_traffic("cliquet_kernel_dsabr1_2p20.md",
+                                                       ["cliquet.cu", "mc.cuh", "sabr_math.cuh"])}
     return res
 
 
