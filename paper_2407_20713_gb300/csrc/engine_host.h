@@ -24,6 +24,9 @@ struct HostProblem {
 sabr_status formula_prepare(const sabr_problem& pr, const sabr_bounds& b, const sabr_cooling& c, uint64_t seed,
                             HostProblem& h);
 // Lanes per chain for a problem of a batch holding batch_chains chains.
+// Tuning override: the environment variable SABR_LANES (a power of two in
+// [1, 32]) sets it for every problem; results then differ only by the FP32
+// rounding of the lane sums.
 int choose_lanes(int n_quotes, int n_mats, int model, long long batch_chains);
 // Dynamic shared memory of a level block (cpb chains) / of an init block.
 size_t level_smem_bytes(int prec, int model, int Q, int M, int cpb);
