@@ -13,6 +13,9 @@ constexpr int kSaBlock = 256;   // threads per SA block (server, init, finalize)
 // batch's chains evenly over the 152 SMs (14 resident per SM at <= 72
 // registers), where 256-thread blocks leave a partly filled second wave.
 constexpr int kLevelBlock = 64;
+// Dynamic shared memory a level block may use: the 227 KB opt-in limit less
+// room for the kernel's static shared memory.
+constexpr size_t kMaxLevelSmem = 226 * 1024;
 constexpr int kStateLen = 12;  // restart x[10], restart f, T0
 
 // One problem of a batch, as the kernels see it (all pointers device).
@@ -53,22 +56,19 @@ struct ProblemDev {
   sabr_result* result;
 };
 
-// The four per-quote inputs of the static formulas, packed so that one
-// 16-byte (FP32) shared-memory load fetches a quote.
+// Per-quote inputs ln(f/K), log2(K f), T and 1/market (FP32) or market
+// (FP64), packed so that one 16-byte (FP32) shared-memory load fetches a
+// quote.
 template <class R> struct __align__(16) QuotePack {
   R lfk, l2kf, T, w;
 };
 
 // Quote tables of one problem staged in shared memory.
 template <class R> struct SmemQuotes {
-  const R* lfk;
-  const R* l2kf;
-  const R* l2k;
-  const R* T;
-  const R* w;
-  const int* mat;
-  const R* mT;
-  const QuotePack<R>* pack;  // (lfk, l2kf, T, w) per quote
+  const QuotePack<R>* pack;  // per quote
+  const R* l2k;              // per quote: log2 K (Oblój)
+  const int* mat;            // per quote: maturity index
+  const R* mT;               // per maturity: T
 };
 
 // Double-float number hi + lo (|lo| <= ulp(hi)/2): sums of FP32 terms carried
@@ -197,9 +197,10 @@ __device__ __forceinline__ typename CostOf<R>::T group_cost(const R* xp, int n_q
     const PolyCoef<R> c1 = expanded_coef<R>(xp, l2f, (R)1);
     const R bw = c1.c0 - c0.c0;  // B / omega
     for (int q = lane; q < n_quotes; q += G) {
+      const QuotePack<R> qp = sq.pack[q];
       PolyCoef<R> c = c0;
-      c.c0 = c0.c0 + bw * sq.T[q];
-      const R r = resid(vol_poly<R>(c, sq.lfk[q]), sq.w[q]);
+      c.c0 = c0.c0 + bw * qp.T;
+      const R r = resid(vol_poly<R>(c, qp.lfk), qp.w);
       acc += r * r;
     }
   } else {
@@ -216,11 +217,12 @@ __device__ __forceinline__ typename CostOf<R>::T group_cost(const R* xp, int n_q
     __syncwarp(gmask);
     for (int q = lane; q < n_quotes; q += G) {
       const int j = sq.mat[q];
+      const QuotePack<R> qp = sq.pack[q];
       PolyCoef<R> c;
       c.c0 = coef[3 * j + 0];
       c.c1 = coef[3 * j + 1];
       c.c2 = coef[3 * j + 2];
-      const R r = resid(vol_poly<R>(c, sq.lfk[q]), sq.w[q]);
+      const R r = resid(vol_poly<R>(c, qp.lfk), qp.w);
       acc += r * r;
     }
     __syncwarp(gmask);

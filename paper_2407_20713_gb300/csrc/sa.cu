@@ -30,24 +30,10 @@ template <class R>
 __device__ __forceinline__ SmemQuotes<R> stage_quotes(const ProblemDev& P, unsigned char* base,
                                                       int nthreads, int tid, unsigned char** end) {
   const int Q = P.n_quotes, M = P.n_mats;
-  R* lfk = (R*)base;
-  R* l2kf = lfk + Q;
-  R* l2k = l2kf + Q;
-  R* T = l2k + Q;
-  R* w = T + Q;
-  R* mT = w + Q;
+  QuotePack<R>* pack = (QuotePack<R>*)base;  // base is 16-byte aligned
+  R* l2k = (R*)(pack + Q);
+  R* mT = l2k + Q;
   int* mat = (int*)(mT + M);
-  for (int i = tid; i < Q; i += nthreads) {
-    lfk[i] = ((const R*)P.q_lfk)[i];
-    l2kf[i] = ((const R*)P.q_l2kf)[i];
-    l2k[i] = ((const R*)P.q_l2k)[i];
-    T[i] = ((const R*)P.q_T)[i];
-    w[i] = ((const R*)P.q_w)[i];
-    mat[i] = P.q_mat[i];
-  }
-  for (int j = tid; j < M; j += nthreads) mT[j] = ((const R*)P.m_T)[j];
-  unsigned char* e = (unsigned char*)(mat + Q);
-  QuotePack<R>* pack = (QuotePack<R>*)(((uintptr_t)e + 15) & ~(uintptr_t)15);
   for (int i = tid; i < Q; i += nthreads) {
     QuotePack<R> qp;
     qp.lfk = ((const R*)P.q_lfk)[i];
@@ -55,9 +41,13 @@ __device__ __forceinline__ SmemQuotes<R> stage_quotes(const ProblemDev& P, unsig
     qp.T = ((const R*)P.q_T)[i];
     qp.w = ((const R*)P.q_w)[i];
     pack[i] = qp;
+    l2k[i] = ((const R*)P.q_l2k)[i];
+    mat[i] = P.q_mat[i];
   }
-  *end = (unsigned char*)(pack + Q);
-  SmemQuotes<R> sq{lfk, l2kf, l2k, T, w, mat, mT, pack};
+  for (int j = tid; j < M; j += nthreads) mT[j] = ((const R*)P.m_T)[j];
+  unsigned char* e = (unsigned char*)(mat + Q);
+  *end = (unsigned char*)(((uintptr_t)e + 15) & ~(uintptr_t)15);
+  SmemQuotes<R> sq{pack, l2k, mat, mT};
   return sq;
 }
 
@@ -526,8 +516,8 @@ int choose_lanes(int n_quotes, int n_mats, int model, long long batch_chains) {
 size_t level_smem_bytes(int prec, int model, int Q, int M, int cpb) {
   const size_t rs = prec == SABR_FP64 ? 8 : 4;
   const size_t cm = (model == SABR_DYN_I || model == SABR_DYN_II) ? (size_t)M : 0;
-  size_t b = (5 * (size_t)Q + M) * rs + 4 * (size_t)Q;
-  b = align_up(b, 16) + 4 * rs * (size_t)Q;  // QuotePack table
+  size_t b = 4 * rs * (size_t)Q + ((size_t)Q + M) * rs + 4 * (size_t)Q;  // pack, l2k, mT, mat
+  b = align_up(b, 16);
   b += (size_t)cpb * 3 * cm * rs + 16 * rs;
   b = align_up(b, 16) + 16;
   b += (size_t)cpb * 8 + (size_t)cpb * kMaxD * rs;
@@ -900,6 +890,11 @@ static sabr_status build_plan(int32_t n, const sabr_problem* problems, const sab
   std::vector<size_t> f_off(nf), mc_off(p->mc.size());
   for (int i = 0; i < nf; ++i) {
     lanes[i] = choose_lanes(hp[i].n_quotes, hp[i].n_mats, hp[i].model, batch_chains);
+    if (level_smem_bytes(hp[i].prec, hp[i].model, hp[i].n_quotes, hp[i].n_mats, kLevelBlock / lanes[i]) >
+        kMaxLevelSmem) {
+      free_plan(p);
+      return fail(SABR_EINVAL, "the quotes of a problem exceed one block's shared memory at its precision");
+    }
     f_off[i] = align_up(o, 256);
     o = formula_layout(hp[i], lanes[i], nullptr, nullptr, f_off[i], pd[i], nullptr, kLevelBlock);
   }

@@ -242,3 +242,29 @@ def test_full_size_dynamic_surface_sampled_against_oracle():
         x0 = 0.5 * (np.asarray(w.lo) + np.asarray(w.hi))
         o_x0 = O.misfit(O.implied_vol(model, x0, 1.0, w.T, w.K), m)
         assert r.misfit_fp64 < o_x0
+
+
+@pytest.mark.parametrize("prec", [sg.FP32, sg.FP64])
+def test_maximum_quote_and_maturity_counts(prec):
+    # 64 maturities x 64 strikes = 4096 quotes, the largest problem the
+    # library accepts, in both precisions (Case I: every maturity has its
+    # own term structure); FP64 follows the oracle's trajectory
+    mats = np.linspace(0.1, 10.0, 64)
+    T = np.repeat(mats, 64)
+    K = np.tile(np.linspace(0.6, 1.5, 64), 64)
+    truth = [0.25, 0.8, -0.5, 0.7, 0.6, 0.9]
+    lo = [0.05, 0.5, -1.0, 0.01, 0.0, 0.0]
+    hi = [0.6, 1.0, 1.0, 1.5, 3.0, 3.0]
+    m = market(O.DYN_I, truth, T, K, seed=5)
+    g, o = run_both(sg.DYN_I, T, K, m, lo, hi, prec=prec, n_chains=3, n_levels=2, chain_len=3, seed=8)
+    assert g.status == 0
+    if prec == sg.FP64:
+        assert g.n_evals == o["n_evals"] and g.n_accepts == o["n_accepts"]
+        np.testing.assert_allclose(g.params, o["params"], rtol=1e-10)
+    o_fit = O.misfit(O.implied_vol(O.DYN_I, g.params, 1.0, T, K), m)
+    assert g.misfit_fp64 == pytest.approx(o_fit, rel=1e-7)
+    # one quote more is refused
+    with pytest.raises(sg.SabrError):
+        sg.calibrate(sg.CalibrationProblem(model=sg.DYN_I, T=np.append(T, 1.0), K=np.append(K, 1.0),
+                                           market=np.append(m, 0.2), lo=lo, hi=hi, prec=prec, n_chains=2,
+                                           n_levels=1, chain_len=1))
