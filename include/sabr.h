@@ -98,8 +98,10 @@ sabr_status sabr_implied_vol(sabr_model model, const double* params,
  * Asynchronous on cuda_stream; the host arrays are read before return.
  * Uses library-owned device scratch (per-block partial sums).  EINVAL for
  * bad sizes, n > 512 options, more than 64 distinct maturities, more than
- * 8192 time steps, or
- * parameters violating rho(t) in [-1,1], nu(t) > 0 on (0, max T].
+ * 8192 time steps, step and option tables beyond one block's shared memory
+ * (the step table takes 16 B a step in FP32 and 32 B in FP64, so FP64 stops
+ * near 5000 steps), or parameters violating rho(t) in [-1,1], nu(t) > 0 on
+ * (0, max T].
  * ------------------------------------------------------------------------ */
 sabr_status sabr_mc_price(sabr_model model, const double* params, double fwd,
                           const double* T, const double* K,

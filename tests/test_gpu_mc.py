@@ -91,3 +91,26 @@ def test_mc_is_deterministic_and_validates():
         sg.mc_price(sg.HAGAN, PARAMS[sg.HAGAN], 1.0, np.ones(513), np.ones(513))
     with pytest.raises(sg.SabrError):
         sg.mc_price(sg.HAGAN, PARAMS[sg.HAGAN], 1.0, [1.0], [1.0], n_paths=1)
+
+
+def test_mc_at_the_size_limits():
+    # 64 maturities x 8 options = 512 (the limit) over 32 years at 250 steps a
+    # year: 8000 steps; FP32 fits one block's shared memory and matches the
+    # oracle on the same streams, FP64 (32 B a step) is refused
+    mats = np.linspace(0.5, 32.0, 64)
+    T = np.repeat(mats, 8)
+    K = np.tile([0.5, 0.8, 0.95, 1.0, 1.05, 1.2, 1.6, 2.5], 64)
+    ic = np.tile([1, 1, 0, 1, 0, 1, 1, 1], 64).astype(np.int8)
+    p = [0.2, 0.7, -0.3, 0.3]
+    ref, _ = O.mc_price(sg.HAGAN, p, 1.0, T, K, is_call=ic, n_paths=777, steps_per_year=250, seed=21, n_threads=8)
+    got, _ = sg.mc_price(sg.HAGAN, p, 1.0, T, K, is_call=ic, n_paths=777, steps_per_year=250, seed=21, prec=sg.FP32)
+    err = np.abs(got.cpu().numpy() - ref)
+    # the FP32 log-state takes one rounding (2^-24 relative) per step, so its
+    # error grows like sqrt(steps): 1e-5 up to 2 years (500 steps), 5e-5 at
+    # 32 years (8000 steps)
+    assert np.max(err[T <= 2.0]) <= TOL[sg.FP32]
+    assert np.max(err) <= 5e-5
+    with pytest.raises(sg.SabrError):
+        sg.mc_price(sg.HAGAN, p, 1.0, T, K, is_call=ic, n_paths=777, steps_per_year=250, seed=21, prec=sg.FP64)
+    with pytest.raises(sg.SabrError):  # one option more
+        sg.mc_price(sg.HAGAN, p, 1.0, np.append(T, 1.0), np.append(K, 1.0), n_paths=777, prec=sg.FP32)
