@@ -30,6 +30,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_LEVELS, CHAIN_LEN, N_CHAINS, FACTOR = 200, 100, 4096, 0.95
+METRIC = "SABR SA cost evals/s (static Hagan surface, 10x21, FP32 bulk)"
+WORKLOAD = ("static Hagan surface: 10 maturities x 21 strikes (each its own smile), 4096 SA chains/smile, "
+            "200 levels x 100 proposals, cooling 0.95")
 # Algorithmic work of one Hagan quote evaluation (eq. haganf + the misfit
 # term), by pipe: (K f)^((1-beta)/2) and its reciprocal (two exp2 of a
 # precomputed log), one square root, one logarithm, two divisions, and about
@@ -210,12 +213,11 @@ def run_reference(args):
     cb["value"] = value
     cb["sample"] = "each step: smile 1 of 10, %d chains, 40 of %d levels x %d proposals" % (N_CHAINS, N_LEVELS,
                                                                                             CHAIN_LEN)
-    line = {"impl": "reference", "metric": "SABR SA cost evals/s (static Hagan surface, 10x21, FP32 bulk)",
+    line = {"impl": "reference", "metric": METRIC,
             "value": value, "unit": "cost-evals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * float(np.mean(dts)), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "static Hagan surface: 10 maturities x 21 strikes, 4096 chains/smile, "
-                                   "200x100 SA", "sampled": True},
+            "config": {"workload": WORKLOAD, "sampled": "each step: smile 1 of 10, 40 of the 200 levels"},
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "cost-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -651,12 +653,11 @@ def run_ours(args):
                 "launch_ms": lvl_ms, "quote_evals_per_launch": quote_evals_per_launch, "peak_from": peak_note,
                 "pipe_rates_per_sm_clk": rates}
 
-    line = {"metric": "SABR SA cost evals/s (static Hagan surface, 10x21, FP32 bulk)", "value": value,
+    line = {"metric": METRIC, "value": value,
             "unit": "cost-evals/s", "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
             "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "static Hagan surface: 10 maturities x 21 strikes (each its own smile), "
-                                   "4096 SA chains/smile, 200 levels x 100 proposals, cooling 0.95",
+            "config": {"workload": WORKLOAD,
                        "l2": "flushed (256 MB write) between timed steps", "precision": "FP32 bulk, FP64 sums"},
             "clocks": clocks, "gpu_launches": int(n_launch * args.steps),
             "e2e": {"value": agg["e2e"], "unit": "cost-evals/s", "h2d_bytes_per_step": h2d,
