@@ -419,12 +419,15 @@ def measure_dynamic(sg, torch, stream, levels=10):
     return res
 
 
-def measure_serving(sg, n_requests, rate_hz):
+def measure_serving(sg, n_requests, rate_hz, formula_only=False):
     """Poisson stream of calibration requests of uneven size (1-12 maturities x
-    5-41 strikes; 80% Hagan / 20% dynamic, 5% MC) through the server."""
+    5-41 strikes; 80% Hagan / 20% dynamic, 5% MC) through the server; with
+    formula_only the MC requests of the stream are left out."""
     import threading
     from paper_2407_20713_gb300 import workloads
     reqs = workloads.serving_stream(n=n_requests, rate_hz=rate_hz)
+    if formula_only:
+        reqs = [q for q in reqs if q.cost == 0]
     probs = []
     for q in reqs:
         sm = q.smile
@@ -508,6 +511,9 @@ def measure_serving_loads(sg, n_requests):
     fp64_rate = n / (time.perf_counter() - t0)
     out = {"capacity": burst}
     out.update(loads)
+    # the 5% MC requests take most of the GPU time of the mix; the formula
+    # requests alone, all at once
+    out["formula_only_capacity"] = measure_serving(sg, n_requests, rate_hz=1e9, formula_only=True)
     out["fp64_one_request_per_launch"] = {"calibrations_per_s": fp64_rate, "sample": "%d formula requests" % n}
     return out
 

@@ -156,10 +156,10 @@ __device__ __forceinline__ void case2_group_coef(const R* xp, int n_mats, R l2f,
     for (int j = 0; j < n_mats; ++j) {
       const R T = sq.mT[j];
       const R A = (R)xp[4] * T, B = (R)xp[5] * T, Qr = (R)xp[8] * T, Qn = (R)xp[9] * T;
-      const int nodes = case2_panels<R>(A, B) * Tr<R>::kGauss;
+      const Eta2Rule<R> rule(A, B);
+      const int nodes = rule.nodes();
       R part = (R)0;
-      for (int k = lane; k < nodes; k += G)
-        part += case2_eta2_node<R>(k, nodes / Tr<R>::kGauss, rho0, nu0, A, B, dr, dn, Qr, Qn);
+      for (int k = lane; k < nodes; k += G) part += rule.node(k, rho0, nu0, A, B, dr, dn, Qr, Qn);
       for (int off = G >> 1; off > 0; off >>= 1) part += __shfl_xor_sync(gmask, part, off);
       if (lane == (j & (G - 1))) {
         const PolyCoef<R> c = dynamic_poly<R>((R)xp[0], (R)xp[1], l2f, T, coef[3 * j + 0], coef[3 * j + 1],
