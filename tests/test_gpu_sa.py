@@ -268,3 +268,23 @@ def test_maximum_quote_and_maturity_counts(prec):
         sg.calibrate(sg.CalibrationProblem(model=sg.DYN_I, T=np.append(T, 1.0), K=np.append(K, 1.0),
                                            market=np.append(m, 0.2), lo=lo, hi=hi, prec=prec, n_chains=2,
                                            n_levels=1, chain_len=1))
+
+
+def test_fp32_and_fp64_outcomes_have_the_same_distribution_over_seeds():
+    # the end point of the SA on these smiles depends on the trajectory (the
+    # spread over seeds is 2-20x within one precision), so FP32 is compared
+    # with FP64 in distribution: 12 seeds each at the headline's size
+    from paper_2407_20713_gb300 import workloads
+    smiles = workloads.static_surface()
+    for i in (0, 9):
+        sm = smiles[i]
+        m = O.implied_vol(O.HAGAN, sm.truth, 1.0, sm.T, sm.K) + sm.noise
+        out = {}
+        for prec in (sg.FP32, sg.FP64):
+            pbs = [sg.CalibrationProblem(model=sg.HAGAN, T=sm.T, K=sm.K, market=m, lo=sm.lo, hi=sm.hi, prec=prec,
+                                         n_chains=sm.n_chains, n_levels=200, chain_len=100, factor=0.95,
+                                         seed=1000 + s) for s in range(12)]
+            out[prec] = np.array([r.misfit_fp64 for r in sg.calibrate_batch(pbs)])
+        med32, med64 = np.median(out[sg.FP32]), np.median(out[sg.FP64])
+        assert 0.7 <= med32 / med64 <= 1.43, (i, med32, med64)
+        assert out[sg.FP32].min() <= 1.1 * out[sg.FP64].min(), (i, out[sg.FP32].min(), out[sg.FP64].min())
