@@ -58,7 +58,9 @@ typedef enum {
 } sabr_cost;
 
 typedef enum {
-  SABR_FP32 = 0, /* FP32 bulk arithmetic, FP64 misfit sums and re-score */
+  SABR_FP32 = 0, /* FP32 bulk arithmetic; misfit sums across lanes in  */
+                 /* double-float (FP32 pairs), MC payoff sums in FP64,  */
+                 /* FP64 re-score of the returned point                 */
   SABR_FP64 = 1  /* FP64 throughout                                     */
 } sabr_precision;
 
@@ -235,7 +237,13 @@ typedef struct {
  * with key = seed and counter (c, k, j, 0x53410000 + block).  Out-of-box
  * (and, for DYN_II, infeasible) proposals are rejected without a cost
  * evaluation.  Blocking: returns when *out is filled.  Results depend only on
- * (problem, bounds, cooling, seed), never on batch mix or launch shape.
+ * (problem, bounds, cooling, seed) and G, the lanes that share a chain's
+ * quotes (the order of the misfit's partial sums), never on the rest of the
+ * batch, slots or launch shape.  G is chosen from the problem and the total
+ * chain count of its batch (more lanes when the batch is small), so a
+ * problem calibrated alone and inside a large batch may differ in the last
+ * bits of its sums when its G differs; the environment variable SABR_LANES
+ * fixes G for every problem.
  * ------------------------------------------------------------------------ */
 sabr_status sabr_calibrate(const sabr_problem* problem,
                            const sabr_bounds* bounds,
@@ -279,7 +287,8 @@ void sabr_plan_destroy(sabr_plan* plan);
  * resident MC-cost request by one proposal wave on a second stream, so that
  * requests that arrive while others run join them on the device.  Finished
  * requests release their memory at once.  A request's result does not depend
- * on what else is resident (same result as sabr_calibrate).
+ * on what else is resident: it is the result of sabr_calibrate on that
+ * request alone (G chosen from the request alone).
  * ------------------------------------------------------------------------ */
 typedef struct {
   int64_t device_bytes; /* pool for resident requests (>= 1 MiB)          */
