@@ -1,13 +1,14 @@
 // sa.cu -- synchronous parallel Simulated Annealing (Sec. 5) on the GPU.
 //
 // Work decomposition: a chain is a group of G lanes (G = 1..32, a power of
-// two); lanes split the quotes of the cost function.  A 256-thread block
-// holds 256/G chains of one problem.  One launch of sa_level_kernel runs one
-// temperature level (chain_len Metropolis steps per chain) for every chain of
-// every problem of a launch group; the chains' states live in registers for
-// the whole level.  At the end of the level each block writes the argmin of
-// its chains' final states, and the last block of a problem to finish (an
-// atomic ticket) reduces the block minima in block order and writes the
+// two); lanes split the quotes of the cost function.  A block holds
+// blockDim/G chains of one problem (64-thread blocks in plans, 256 in the
+// server).  One launch of sa_level_kernel runs one temperature level
+// (chain_len Metropolis steps per chain) for every chain of every problem of
+// a launch group; the chains' states live in registers for the whole level.
+// At the end of the level each block writes the argmin of its chains' final
+// states, and the last block of a problem to finish (an atomic ticket) takes
+// the argmin over the block minima (lowest block on a tie) and writes the
 // restart point of the next level.  No block ever waits for another.
 #include <algorithm>
 #include <cmath>
@@ -137,7 +138,6 @@ __global__ void sa_init_kernel(const ProblemDev* __restrict__ probs, const int* 
 // Every thread of the block calls this.
 template <class R, int MODEL>
 __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int level, unsigned char* smem) {
-  const int2 bm = make_int2(0, blk);
   unsigned char* rest;
   const SmemQuotes<R> sq = stage_quotes<R>(P, smem, blockDim.x, threadIdx.x, &rest);
   constexpr int D = Dim<MODEL>::value;
@@ -151,7 +151,7 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
   R* red_x = (R*)(red_f + cpb);
   __syncthreads();
 
-  const int chain = bm.y * cpb + g;
+  const int chain = blk * cpb + g;
   const bool active = chain < P.n_chains;
   const unsigned gmask = group_mask(G);
 
@@ -288,9 +288,9 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
     for (int c = threadIdx.x; c < cpb; c += 32) argmin_merge(fb, best, red_f[c], c);
     warp_argmin(fb, best);
     if (threadIdx.x == 0) {
-      P.part_f[bm.y] = fb;
-      P.part_c[bm.y] = bm.y * cpb + best;
-      for (int i = 0; i < kMaxD; ++i) P.part_x[(size_t)bm.y * kMaxD + i] = (double)red_x[best * kMaxD + i];
+      P.part_f[blk] = fb;
+      P.part_c[blk] = blk * cpb + best;
+      for (int i = 0; i < kMaxD; ++i) P.part_x[(size_t)blk * kMaxD + i] = (double)red_x[best * kMaxD + i];
       __threadfence();
       const unsigned ticket = atomicAdd(P.arrive, 1u);
       s_last = ticket == (unsigned)(P.n_blocks - 1);
