@@ -104,3 +104,28 @@ def test_empty_and_invalid_inputs():
         sg.implied_vol(sg.HAGAN, [0.2, 0.5, 1.0, 0.5], 1.0, [1.0], [1.0])
     with pytest.raises(sg.SabrError):
         sg.implied_vol(sg.HAGAN, [0.2, 0.5, 0.0, 0.5], -1.0, [1.0], [1.0])
+
+
+@pytest.mark.parametrize("prec", [sg.FP64, sg.FP32])
+@pytest.mark.parametrize("model", [sg.HAGAN, sg.OBLOJ])
+def test_static_formulas_on_an_extreme_grid(model, prec):
+    # strikes from 5% to 20x the forward, maturities from 4 days to 30 years,
+    # parameters at the edges of their ranges: the branch-free z/x(z) and the
+    # SFU forms must hold their accuracy everywhere the formula is defined
+    K = np.exp(np.linspace(np.log(0.05), np.log(20.0), 41))
+    K = np.concatenate([K, [1.0, 1.0 + 1e-7, 1.0 - 1e-7, 1.0 + 1e-3]])
+    T = np.array([0.01, 1.0, 30.0])
+    TT, KK = np.repeat(T, K.size), np.tile(K, T.size)
+    worst = 0.0
+    for alpha in (0.01, 0.3, 2.0):
+        for beta in (0.0, 0.5, 1.0):
+            for rho in (-0.999, -0.5, 0.0, 0.5, 0.999):
+                for nu in (0.01, 0.5, 3.0):
+                    p = [alpha, beta, rho, nu]
+                    ref = O.implied_vol(model, p, 1.0, TT, KK)
+                    got = sg.implied_vol(model, p, 1.0, TT, KK, prec=prec).cpu().numpy()
+                    ok = np.isfinite(ref) & (ref > 0)
+                    assert np.all(np.isfinite(got[ok])), p
+                    err = np.abs(got[ok] - ref[ok]) / ref[ok]
+                    worst = max(worst, float(err.max()))
+    assert worst <= TOL[prec], worst
