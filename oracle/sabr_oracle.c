@@ -5,6 +5,7 @@
  */
 #include "sabr_oracle.h"
 
+#include <float.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -274,14 +275,19 @@ static double G_fixed(const dyn_ctx* c, double s, double* absint) {
 }
 
 /* Panels for G_fixed: the fewest (a power of two) for which doubling them
- * changes G(T) by no more than 1e-15 of int_0^T |nu rho|. */
+ * changes G(T) by no more than 1e-15 of int_0^T |nu rho|, or by no more than
+ * the rounding of the 10n-term sum itself (8 sqrt(10 n) eps of it): with
+ * fast decay rates (a T, b T of order 100) the change never gets below
+ * 1e-15 once rounding dominates, and the search would otherwise run to 2^16
+ * panels. */
 static int choose_panels(dyn_ctx* c) {
   c->npan = 1;
   double a, g = G_fixed(c, c->T, &a);
   for (int n = 2; n <= (1 << 16); n *= 2) {
     c->npan = n;
     double a2, g2 = G_fixed(c, c->T, &a2);
-    if (fabs(g2 - g) <= 1e-15 * a2 + 1e-300) return n;
+    const double noise = 8.0 * sqrt(10.0 * n) * DBL_EPSILON;
+    if (fabs(g2 - g) <= (noise > 1e-15 ? noise : 1e-15) * a2 + 1e-300) return n;
     g = g2;
   }
   return c->npan;

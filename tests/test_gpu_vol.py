@@ -129,3 +129,33 @@ def test_static_formulas_on_an_extreme_grid(model, prec):
                     err = np.abs(got[ok] - ref[ok]) / ref[ok]
                     worst = max(worst, float(err.max()))
     assert worst <= TOL[prec], worst
+
+
+@pytest.mark.parametrize("prec", [sg.FP64, sg.FP32])
+@pytest.mark.parametrize("model", [sg.DYN_I, sg.DYN_II])
+def test_dynamic_formulas_on_an_extreme_grid(model, prec):
+    # maturities from 4 days to 30 years and decay rates a, b from 0 to 5
+    # (a T, b T up to 150): the Case I series/closed-form switch and the
+    # Case II eta2^2 rules must hold their accuracy
+    K = np.exp(np.linspace(np.log(0.3), np.log(3.0), 15))
+    T = np.array([0.01, 0.25, 1.0, 10.0, 30.0])
+    TT, KK = np.repeat(T, K.size), np.tile(K, T.size)
+    rng = np.random.default_rng(77 + model + 10 * prec)
+    worst, n = 0.0, 0
+    for a in (0.0, 1e-3, 1.0, 5.0):
+        for b in (0.0, 1e-3, 1.0, 5.0):
+            p = [0.25, 0.7, -0.5, 0.8, a, b]
+            if model == sg.DYN_II:
+                while True:
+                    q = p + [rng.uniform(-0.2, 0.2), rng.uniform(0.0, 0.3), rng.uniform(-0.3, 0.3),
+                             rng.uniform(-0.3, 0.3)]
+                    if O.feasible(O.DYN_II, q, 30.0):
+                        p = q
+                        break
+            ref = O.implied_vol(model, p, 1.0, TT, KK)
+            got = sg.implied_vol(model, p, 1.0, TT, KK, prec=prec).cpu().numpy()
+            ok = np.isfinite(ref) & (ref > 0)
+            n += int(ok.sum())
+            assert np.all(np.isfinite(got[ok])), p
+            worst = max(worst, float((np.abs(got[ok] - ref[ok]) / ref[ok]).max()))
+    assert n > 0.8 * 16 * TT.size and worst <= TOL[prec], (n, worst)
