@@ -37,7 +37,8 @@ __global__ void __launch_bounds__(kClqBlock) cliquet_kernel(McDev P, const doubl
   const R log_abs = (R)(P.log_absorb * PathUnits<R>::kLogUnit);
   const R fl = (R)floor_l, cl = (R)cap_l;
   double s1 = 0.0, s2 = 0.0;
-  // two paths per thread (path, path + stride) advance together
+  // kMcPathsPerThread paths per thread (path, path + stride, ...) advance
+  // together
   constexpr int NPT = kMcPathsPerThread;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p0 < P.n_paths; p0 += NPT * stride) {
@@ -170,7 +171,7 @@ extern "C" sabr_status sabr_mc_cliquet(sabr_model model, const double* params, d
                       (size_t)n_resets * sizeof(int);
   if (smem > 200 * 1024) return fail(SABR_EINVAL, "too many time steps for one launch");
   // resident blocks of the GPU (grid-stride; no partly filled second wave),
-  // and no more than the paths need at two paths per thread
+  // and no more than the paths need at kMcPathsPerThread paths per thread
   int per_sm = 8;
   if (prec == SABR_FP64) {
     cudaFuncSetAttribute(cliquet_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
