@@ -123,28 +123,6 @@ __global__ void cliquet_reduce_kernel(const double* __restrict__ partial, int bl
   if (se) *se = disc * sqrt(var / N);
 }
 
-// rho(t) in [-1, 1] and nu(t) > 0 on [0, T] for Case II parameters: the
-// extremes of (c + q t) e^{-k t} + d lie at the ends or at t* = 1/k - c/q.
-static bool cliquet_feasible(int model, const double* x, double T) {
-  if (model != SABR_DYN_II) return true;
-  double mn[2], mx[2];
-  const double c[2] = {x[2], x[3]}, q[2] = {x[8], x[9]}, k[2] = {x[4], x[5]}, d[2] = {x[6], x[7]};
-  for (int j = 0; j < 2; ++j) {
-    const double g0 = c[j] + d[j], g1 = (c[j] + q[j] * T) * std::exp(-k[j] * T) + d[j];
-    mn[j] = std::min(g0, g1);
-    mx[j] = std::max(g0, g1);
-    if (k[j] != 0.0 && q[j] != 0.0) {
-      const double ts = 1.0 / k[j] - c[j] / q[j];
-      if (ts > 0.0 && ts < T) {
-        const double gs = (c[j] + q[j] * ts) * std::exp(-k[j] * ts) + d[j];
-        mn[j] = std::min(mn[j], gs);
-        mx[j] = std::max(mx[j], gs);
-      }
-    }
-  }
-  return mn[0] >= -1.0 && mx[0] <= 1.0 && mn[1] > 0.0;
-}
-
 }  // namespace sabr
 
 extern "C" sabr_status sabr_mc_cliquet(sabr_model model, const double* params, double fwd, double T,
@@ -161,7 +139,8 @@ extern "C" sabr_status sabr_mc_cliquet(sabr_model model, const double* params, d
   if (!(floor_local <= cap_local) || !(floor_global <= cap_global) || !std::isfinite(discount))
     return fail(SABR_EINVAL, "need floor <= cap (local and global) and a finite discount");
   if (n_paths < 2) return fail(SABR_EINVAL, "n_paths must be >= 2");
-  if (!cliquet_feasible(model, params, T)) return fail(SABR_EINVAL, "parameters violate rho(t) in [-1,1], nu(t) > 0");
+  if (model == SABR_DYN_II && !case2_feasible<double, double>(params, T))
+    return fail(SABR_EINVAL, "parameters violate rho(t) in [-1,1], nu(t) > 0");
   std::vector<double> resets(n_resets), K(n_resets, fwd);
   for (int i = 0; i < n_resets; ++i) resets[i] = (double)(i + 1) * T / n_resets;
   McHost h;

@@ -118,27 +118,6 @@ __global__ void mc_reduce_kernel(McDev P, int n_sets, int blocks_per_set, const 
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-static bool host_feasible(int model, const double* x, double Tmax) {
-  if (model != SABR_DYN_II) return true;
-  auto range = [&](double c, double q, double k, double d, double& mn, double& mx) {
-    double g0 = c + d, g1 = (c + q * Tmax) * std::exp(-k * Tmax) + d;
-    mn = std::min(g0, g1);
-    mx = std::max(g0, g1);
-    if (k != 0.0 && q != 0.0) {
-      double ts = 1.0 / k - c / q;
-      if (ts > 0.0 && ts < Tmax) {
-        double gs = (c + q * ts) * std::exp(-k * ts) + d;
-        mn = std::min(mn, gs);
-        mx = std::max(mx, gs);
-      }
-    }
-  };
-  double rmn, rmx, nmn, nmx;
-  range(x[2], x[8], x[4], x[6], rmn, rmx);
-  range(x[3], x[9], x[5], x[7], nmn, nmx);
-  return rmn >= -1.0 && rmx <= 1.0 && nmn > 0.0;
-}
-
 sabr_status mc_prepare(int model, double fwd, const double* T, const double* K, const int8_t* is_call,
                        const double* discount, int64_t n, int64_t n_paths, double spy, uint64_t seed,
                        int prec, McHost& h) {
@@ -369,7 +348,7 @@ extern "C" sabr_status sabr_mc_price(sabr_model model, const double* params, dou
   if (!price_out) return fail(SABR_EINVAL, "price_out is NULL");
   McHost h;
   SABR_TRY(mc_prepare(model, fwd, T, K, is_call, discount, n, n_paths, steps_per_year, seed, prec, h));
-  if (!host_feasible(model, params, h.Tmax))
+  if (model == SABR_DYN_II && !case2_feasible<double, double>(params, h.Tmax))
     return fail(SABR_EINVAL, "parameters violate rho(t) in [-1,1], nu(t) > 0");
   const int bps = mc_blocks_per_set(h, 1);
   const size_t img = mc_image_bytes(h);

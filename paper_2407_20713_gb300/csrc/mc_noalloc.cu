@@ -52,28 +52,6 @@ static sabr_status noalloc_scratch(int dev, unsigned char** ptr) {
   return SABR_OK;
 }
 
-// rho(t) in [-1, 1] and nu(t) > 0 on [0, Tmax] for Case II parameters: the
-// extremes of (c + q t) e^{-k t} + d lie at the ends or at t* = 1/k - c/q.
-static bool noalloc_feasible(int model, const double* x, double Tmax) {
-  if (model != SABR_DYN_II) return true;
-  double mn[2], mx[2];
-  const double c[2] = {x[2], x[3]}, q[2] = {x[8], x[9]}, k[2] = {x[4], x[5]}, d[2] = {x[6], x[7]};
-  for (int j = 0; j < 2; ++j) {
-    const double g0 = c[j] + d[j], g1 = (c[j] + q[j] * Tmax) * std::exp(-k[j] * Tmax) + d[j];
-    mn[j] = g0 < g1 ? g0 : g1;
-    mx[j] = g0 < g1 ? g1 : g0;
-    if (k[j] != 0.0 && q[j] != 0.0) {
-      const double ts = 1.0 / k[j] - c[j] / q[j];
-      if (ts > 0.0 && ts < Tmax) {
-        const double gs = (c[j] + q[j] * ts) * std::exp(-k[j] * ts) + d[j];
-        mn[j] = gs < mn[j] ? gs : mn[j];
-        mx[j] = gs > mx[j] ? gs : mx[j];
-      }
-    }
-  }
-  return mn[0] >= -1.0 && mx[0] <= 1.0 && mn[1] > 0.0;
-}
-
 }  // namespace sabr
 
 extern "C" sabr_status sabr_mc_price_noalloc(sabr_model model, const double* params, double fwd, const double* T,
@@ -87,7 +65,7 @@ extern "C" sabr_status sabr_mc_price_noalloc(sabr_model model, const double* par
   if (!price_out) return fail(SABR_EINVAL, "price_out is NULL");
   McHost h;
   SABR_TRY(mc_prepare(model, fwd, T, K, is_call, discount, n, n_paths, steps_per_year, seed, prec, h));
-  if (!noalloc_feasible(model, params, h.Tmax))
+  if (model == SABR_DYN_II && !case2_feasible<double, double>(params, h.Tmax))
     return fail(SABR_EINVAL, "parameters violate rho(t) in [-1,1], nu(t) > 0");
   // a fixed grid (at most 1216 blocks), independent of the occupancy the
   // pricing kernel reaches, so the scratch bound below is a property of the

@@ -462,28 +462,6 @@ __global__ void __launch_bounds__(kSaBlock) sa_finalize_kernel(const ProblemDev*
 // ---------------------------------------------------------------------------
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Host copy of the Case II range test (feasibility of x0).
-static void h_range(double c, double q, double k, double d, double Tmax, double& mn, double& mx) {
-  double g0 = c + d, g1 = (c + q * Tmax) * std::exp(-k * Tmax) + d;
-  mn = std::min(g0, g1);
-  mx = std::max(g0, g1);
-  if (k != 0.0 && q != 0.0) {
-    double ts = 1.0 / k - c / q;
-    if (ts > 0.0 && ts < Tmax) {
-      double gs = (c + q * ts) * std::exp(-k * ts) + d;
-      mn = std::min(mn, gs);
-      mx = std::max(mx, gs);
-    }
-  }
-}
-static bool h_feasible(int model, const double* x, double Tmax) {
-  if (model != SABR_DYN_II) return true;
-  double rmn, rmx, nmn, nmx;
-  h_range(x[2], x[8], x[4], x[6], Tmax, rmn, rmx);
-  h_range(x[3], x[9], x[5], x[7], Tmax, nmn, nmx);
-  return rmn >= -1.0 && rmx <= 1.0 && nmn > 0.0;
-}
-
 static int next_pow2(int v) {
   int p = 1;
   while (p < v) p <<= 1;
@@ -588,7 +566,8 @@ sabr_status formula_prepare(const sabr_problem& pr, const sabr_bounds& b, const 
     h.x0[i] = i < h.d ? (pr.x0 ? pr.x0[i] : 0.5 * (h.lo[i] + h.hi[i])) : 0.0;
     if (h.x0[i] < h.lo[i] || h.x0[i] > h.hi[i]) return fail(SABR_EINVAL, "x0 outside the box");
   }
-  if (!h_feasible(h.model, h.x0, h.Tmax)) return fail(SABR_EINVAL, "x0 violates the Case II constraints");
+  if (h.model == SABR_DYN_II && !case2_feasible<double, double>(h.x0, h.Tmax))
+    return fail(SABR_EINVAL, "x0 violates the Case II constraints");
   h.ck.resize(std::max(h.n_levels, 1));
   for (int k = 0; k < h.n_levels; ++k) h.ck[k] = std::pow(c.factor, (double)k);
   return SABR_OK;

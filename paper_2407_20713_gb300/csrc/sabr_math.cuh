@@ -8,6 +8,7 @@
 //    eq. (integrales_SABRd) for Case I (eq. el_fun_1) and Case II
 //    (eq. el_fun_3), and the per-maturity polynomial of eq. (vola_SABRd).
 #pragma once
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -592,24 +593,33 @@ __device__ __forceinline__ PolyCoef<R> dynamic_coef(const P* x, R l2f, R T) {
 
 // Case II feasibility: rho(t) in [-1, 1], nu(t) > 0 on [0, Tmax] (extremes
 // at the ends or at the stationary point t* = 1/k - c/q of
-// g(t) = (c + q t) e^{-k t} + d).
+// g(t) = (c + q t) e^{-k t} + d).  Host and device: the library checks x0
+// and the parameters of its pricers on the host with the same code the
+// kernels use to reject proposals.
+template <class R> __host__ __device__ __forceinline__ R hd_exp(R x) {
+#ifdef __CUDA_ARCH__
+  return m_exp(x);
+#else
+  return std::exp(x);
+#endif
+}
 template <class R>
-__device__ __forceinline__ void g_range(R c, R q, R k, R d, R Tmax, R& gmin, R& gmax) {
+__host__ __device__ __forceinline__ void g_range(R c, R q, R k, R d, R Tmax, R& gmin, R& gmax) {
   const R g0 = c + d;
-  const R g1 = (c + q * Tmax) * m_exp(-k * Tmax) + d;
+  const R g1 = (c + q * Tmax) * hd_exp(-k * Tmax) + d;
   gmin = g0 < g1 ? g0 : g1;
   gmax = g0 < g1 ? g1 : g0;
   if (k != (R)0 && q != (R)0) {
     const R ts = (R)1 / k - c / q;
     if (ts > (R)0 && ts < Tmax) {
-      const R gs = (c + q * ts) * m_exp(-k * ts) + d;
+      const R gs = (c + q * ts) * hd_exp(-k * ts) + d;
       gmin = gs < gmin ? gs : gmin;
       gmax = gs > gmax ? gs : gmax;
     }
   }
 }
 template <class R, class P>
-__device__ __forceinline__ bool case2_feasible(const P* x, R Tmax) {
+__host__ __device__ __forceinline__ bool case2_feasible(const P* x, R Tmax) {
   R rmin, rmax, nmin, nmax;
   g_range<R>((R)x[2], (R)x[8], (R)x[4], (R)x[6], Tmax, rmin, rmax);
   g_range<R>((R)x[3], (R)x[9], (R)x[5], (R)x[7], Tmax, nmin, nmax);
