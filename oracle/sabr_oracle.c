@@ -691,19 +691,27 @@ static double sa_cost(const sa_ctx* c, const double* x, double* scratch) {
   return orc_misfit(scratch, c->mkt, c->n);
 }
 
-/* The uniforms of proposal (chain, level, step): word j of Philox block
- * j/4 with counter (chain, level, step, TAG_SA + j/4). */
+/* The uniforms of proposal (chain, level, step) of a d-parameter model.
+ * Word j (j < d) is word j%4 of the Philox block with counter
+ * (chain, level, step, TAG_SA + j/4); u[j] = orc_u01(word j) moves
+ * parameter j.  orc_u01 keeps the top 23 bits of a word, so words 0, 1, 2
+ * carry 9 + 9 + 9 unused low bits; the acceptance uniform u[d] is the 23-bit
+ * integer whose bits, high to low, are the low 9 bits of word 0, the low 9
+ * of word 1 and the low 5 of word 2, mapped like any other 23-bit draw. */
 static void sa_uniforms(const uint32_t key[2], int chain, int level, int step,
-                        int count, double* u) {
-  uint32_t w[4];
-  for (int j = 0; j < count; ++j) {
+                        int d, double* u) {
+  uint32_t w[4], spare[3] = {0u, 0u, 0u};
+  for (int j = 0; j < d; ++j) {
     if ((j & 3) == 0) {
       uint32_t ctr[4] = {(uint32_t)chain, (uint32_t)level, (uint32_t)step,
                          ORC_TAG_SA + (uint32_t)(j >> 2)};
       orc_philox4x32_10(ctr, key, w);
     }
     u[j] = orc_u01(w[j & 3]);
+    if (j < 3) spare[j] = w[j & 3] % 512u; /* the bits below the top 23 */
   }
+  uint32_t bits = spare[0] * 16384u + spare[1] * 32u + spare[2] % 32u;
+  u[d] = ((double)bits + 0.5) * 0x1p-23;
 }
 
 int orc_sa_calibrate(int model, int cost, double f, int64_t n,
@@ -766,7 +774,7 @@ int orc_sa_calibrate(int model, int cost, double f, int64_t n,
       double* scr = scratch + n * ch;
       double u[11], xp[10];
       for (int st = 0; st < chain_len; ++st) {
-        sa_uniforms(key, ch, lev, st, d + 1, u);
+        sa_uniforms(key, ch, lev, st, d, u);
         int inside = 1;
         for (int i = 0; i < 10; ++i) xp[i] = 0.0;
         for (int i = 0; i < d; ++i) {

@@ -52,16 +52,24 @@ __global__ void mcsa_init_kernel(McSaDev P) {
   }
 }
 
+// u[0 .. d-1]: move uniforms, u[d]: acceptance uniform (sa_accept_word).
 __device__ __forceinline__ void wave_uniforms(const McSaDev& P, int chain, int level, int st, double* u) {
-  const int nb = (P.d + 4) / 4;
+  const int nb = sa_philox_blocks(P.d);
+  uint32_t w0 = 0, w1 = 0, w2 = 0;
   for (int b = 0; b < nb; ++b) {
     const uint4 w = philox4x32_10(make_uint4((uint32_t)chain, (uint32_t)level, (uint32_t)st, kTagSA + (uint32_t)b),
                                   P.key0, P.key1);
+    if (b == 0) {
+      w0 = w.x;
+      w1 = w.y;
+      w2 = w.z;
+    }
     u[4 * b + 0] = u01<double>(w.x);
     u[4 * b + 1] = u01<double>(w.y);
     u[4 * b + 2] = u01<double>(w.z);
     u[4 * b + 3] = u01<double>(w.w);
   }
+  u[P.d] = u01<double>(sa_accept_word(w0, w1, w2));
 }
 
 __device__ __forceinline__ double level_step(const McSaDev& P, int level, double* Tk) {

@@ -196,17 +196,18 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
 
   if (active) {
     uint4 wbuf = make_uint4(0u, 0u, 0u, 0u);
-    constexpr int NB = (D + 4) / 4;       // Philox blocks per step
+    constexpr int NB = sa_philox_blocks(D);  // Philox blocks per step
     const int S = G >= NB ? G / NB : 1;  // steps per batch of Philox blocks
     int s_ctr = 0;                         // st mod S
     for (int st = 0; st < P.chain_len; ++st) {
-      // D move uniforms and one acceptance uniform: words 0..D of Philox
-      // blocks 0, 1, ... with counter (chain, level, step, tag + block).
-      // With G >= NB lanes, the chain's lanes compute the blocks of S = G/NB
-      // consecutive steps at once (lane l: step st0 + l/NB, block l%NB) and
-      // every step gathers its words by shuffles; otherwise each lane
-      // computes all NB blocks of every step.
-      R u[4 * NB];
+      // D Philox words of blocks 0, 1, ... with counter (chain, level, step,
+      // tag + block): D move uniforms and, from their unused low bits, the
+      // acceptance uniform (sa_accept_word).  With G >= NB lanes, the chain's
+      // lanes compute the blocks of S = G/NB consecutive steps at once
+      // (lane l: step st0 + l/NB, block l%NB) and every step gathers its
+      // words by shuffles; otherwise each lane computes all NB blocks of
+      // every step.
+      uint32_t wv[4 * NB];
       if (G >= NB) {
         const int s_in = s_ctr;
         s_ctr = s_ctr + 1 == S ? 0 : s_ctr + 1;
@@ -218,10 +219,10 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
         }
         const int base = ((threadIdx.x & 31) & ~(G - 1)) + s_in * NB;
 #pragma unroll
-        for (int i = 0; i <= D; ++i) {
+        for (int i = 0; i < D; ++i) {
           const uint32_t word =
               (i & 3) == 0 ? wbuf.x : ((i & 3) == 1 ? wbuf.y : ((i & 3) == 2 ? wbuf.z : wbuf.w));
-          u[i] = u01<R>(__shfl_sync(gmask, word, base + (i >> 2)));
+          wv[i] = __shfl_sync(gmask, word, base + (i >> 2));
         }
       } else {
 #pragma unroll
@@ -229,12 +230,16 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
           const uint4 w = philox4x32_10(
               make_uint4((uint32_t)chain, (uint32_t)level, (uint32_t)st, kTagSA + (uint32_t)b), P.key0,
               P.key1);
-          u[4 * b + 0] = u01<R>(w.x);
-          u[4 * b + 1] = u01<R>(w.y);
-          u[4 * b + 2] = u01<R>(w.z);
-          u[4 * b + 3] = u01<R>(w.w);
+          wv[4 * b + 0] = w.x;
+          wv[4 * b + 1] = w.y;
+          wv[4 * b + 2] = w.z;
+          wv[4 * b + 3] = w.w;
         }
       }
+      R u[D + 1];
+#pragma unroll
+      for (int i = 0; i < D; ++i) u[i] = u01<R>(wv[i]);
+      u[D] = u01<R>(sa_accept_word(wv[0], wv[1], wv[2]));
       R xp[D];
       bool inside = true;
 #pragma unroll

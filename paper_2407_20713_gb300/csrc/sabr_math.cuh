@@ -135,6 +135,17 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 constexpr uint32_t kTagSA = 0x53410000u;
 constexpr uint32_t kTagMC = 0x4D430000u;
 
+// SA proposal (chain, level, step) of a d-parameter model draws words
+// 0 .. d-1 of Philox blocks (chain, level, step, kTagSA + j/4), j = word:
+// the high 23 bits of word i move parameter i, and the acceptance uniform is
+// the 23 bits the moves leave unused in words 0, 1 and 2 (low 9, 9 and 5
+// bits), packed as the high bits of one word.  A static model (d = 4) needs
+// one Philox block per proposal.
+constexpr int sa_philox_blocks(int d) { return (d + 3) / 4; }
+__device__ __forceinline__ uint32_t sa_accept_word(uint32_t w0, uint32_t w1, uint32_t w2) {
+  return ((w0 & 0x1FFu) << 23) | ((w1 & 0x1FFu) << 14) | ((w2 & 0x1Fu) << 9);
+}
+
 // 23 random bits + 1/2, scaled by 2^-23: exact in float, strictly in (0,1).
 // Written as one fused multiply-add, (w >> 9) 2^-23 + 2^-24, whose product
 // and sum are both exact, so the value is the same.
@@ -147,24 +158,40 @@ template <class R> __device__ __forceinline__ R u01(uint32_t w) {
 // D = sqrt(1 - 2 rho z + z^2) = sqrt((z - rho)^2 + (1 - rho)(1 + rho)).
 // Since (D + z - rho)(D - z + rho) = (1 - rho)(1 + rho), also
 // u = (1 + rho)/(D - z + rho); the first form has no cancellation for
-// z >= rho, the second none for z <= rho, so u is one division of selected
-// operands.  Near z = 0, ln u alone loses the relative accuracy of x, and
-// Goldberg's identity ln(1 + w) = w ln(u)/(u - 1) (u the rounded 1 + w) is
-// used with w = u - 1 = 2 z/(1 - z + D), i.e.
+// z >= rho, the second none for z <= rho.  Both are D + |z - rho| over a
+// constant or a constant over it.  The per-proposal constants of rho are
+// kept in ZxConst.
+// ---------------------------------------------------------------------------
+template <class R> struct ZxConst {
+  R rho, omr, opr, q0;  // rho, 1 - rho, 1 + rho, (1 - rho)(1 + rho)
+  R ln_opr, ln_omr;     // ln(1 + rho), ln(1 - rho) (FP32 form only)
+};
+// omr = 1 - rho and opr = 1 + rho are formed from the FP64 parameter.
+template <class R, class P> __device__ __forceinline__ ZxConst<R> zx_setup(P rho) {
+  ZxConst<R> c;
+  c.rho = (R)rho;
+  c.omr = (R)(1.0 - (double)rho);
+  c.opr = (R)(1.0 + (double)rho);
+  c.q0 = c.omr * c.opr;
+  c.ln_opr = c.ln_omr = (R)0;
+  return c;
+}
+
+// FP64 form: u is one division of selected operands.  Near z = 0, ln u alone
+// loses the relative accuracy of x, and Goldberg's identity
+// ln(1 + w) = w ln(u)/(u - 1) (u the rounded 1 + w) is used with
+// w = u - 1 = 2 z/(1 - z + D), i.e.
 //     z / x = (u - 1)(1 - z + D) / (2 ln u)     (z/w = (1 - z + D)/2),
 // and z / x = (1 - z + D)/2 when u rounds to 1.  Every lane runs the same
 // instructions whatever the sign and size of z (selects, no branches).
-// omr = 1 - rho and opr = 1 + rho are passed in, formed from the FP64
-// parameter.  The result is returned as a quotient zn / xd so callers fold
-// it into their own single division.  This is the FP64 form; the FP32 form
-// (a specialisation below) avoids the library logarithm.
-// ---------------------------------------------------------------------------
+// The result is returned as a quotient zn / xd so callers fold it into their
+// own single division.
 template <class R>
-__device__ __forceinline__ void z_over_x_parts(R z, R rho, R omr, R opr, R& zn, R& xd) {
-  const R zr = z - rho;
-  const R D = m_sqrt_pos(zr * zr + omr * opr);
-  const bool low = z <= rho;
-  const R u = m_div(low ? opr : D + zr, low ? D - zr : omr);
+__device__ __forceinline__ void z_over_x_parts(R z, const ZxConst<R>& c, R& zn, R& xd) {
+  const R zr = z - c.rho;
+  const R D = m_sqrt_pos(zr * zr + c.q0);
+  const bool low = z <= c.rho;
+  const R u = m_div(low ? c.opr : D + zr, low ? D - zr : c.omr);
   const R L = m_log(u);
   const R um1 = u - (R)1;
   const R half_w_inv = ((R)1 - z + D) * (R)0.5;  // z / w
@@ -176,46 +203,50 @@ __device__ __forceinline__ void z_over_x_parts(R z, R rho, R omr, R opr, R& zn, 
 
 // FP32 form.  With t = (u - 1)/(u + 1) = z/(1 + D) (|t| < 1; from the form
 // of u above), x = ln u = 2 atanh t, so z/x = (1 + D)/(2 S(t^2)) where
-// S(t^2) = atanh(t)/t = sum_k t^(2k)/(2k + 1).  For |t| < 1/4 (|x| < 0.51)
-// the series to t^12 is exact to 2e-10 relative; elsewhere |x| > 0.51 and
-// x = ln u from the SFU log2 (absolute error about 2^-22) is accurate to a
-// few 1e-7 relative.  Both are formed and one is selected, so no lane
-// branches; FP32 emulation against 50-digit values (with the SFU error
-// added) gives a worst relative error of 6.2e-7 over z in [-20, 20],
-// rho in [-0.999, 0.999].
+// S(t^2) = atanh(t)/t = sum_k t^(2k)/(2k + 1).  For |t| < 1/5 (|x| < 0.41)
+// the series to t^8 is exact to 1e-8 relative.  Elsewhere |x| > 0.40 and
+// x = ln u = +-(ln(D + |z - rho|) - ln(1 -+ rho)), the first logarithm from
+// the SFU log2 (absolute error about 2^-22) and the second a per-proposal
+// constant, is accurate to a few 1e-7 relative.  Both are formed and one is
+// selected, so no lane branches; FP32 emulation against the FP64 formula
+// (with the SFU errors added) gives a worst relative error below 1e-6 over
+// z in [-20, 20], rho in [-0.999999, 0.999999].
 __device__ __forceinline__ float lg2_approx(float x) {
   float y;
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+template <> __device__ __forceinline__ ZxConst<float> zx_setup<float, double>(double rho) {
+  ZxConst<float> c;
+  c.rho = (float)rho;
+  c.omr = (float)(1.0 - rho);
+  c.opr = (float)(1.0 + rho);
+  c.q0 = c.omr * c.opr;
+  c.ln_opr = lg2_approx(c.opr) * 0.69314718055994531f;
+  c.ln_omr = lg2_approx(c.omr) * 0.69314718055994531f;
+  return c;
+}
+template <> __device__ __forceinline__ ZxConst<float> zx_setup<float, float>(float rho) {
+  return zx_setup<float, double>((double)rho);
+}
 template <>
-__device__ __forceinline__ void z_over_x_parts<float>(float z, float rho, float omr, float opr, float& zn,
-                                                      float& xd) {
-  const float zr = z - rho;
-  const float D = m_sqrt_pos(zr * zr + omr * opr);
+__device__ __forceinline__ void z_over_x_parts<float>(float z, const ZxConst<float>& c, float& zn, float& xd) {
+  const float zr = z - c.rho;
+  const float D = m_sqrt_pos(zr * zr + c.q0);
   const float onepD = 1.0f + D;
   const float t = __fdividef(z, onepD);
   const float t2 = t * t;
-  float S = 1.0f / 13.0f;
-  S = S * t2 + 1.0f / 11.0f;
-  S = S * t2 + 1.0f / 9.0f;
-  S = S * t2 + 1.0f / 7.0f;
-  S = S * t2 + 1.0f / 5.0f;
-  S = S * t2 + 1.0f / 3.0f;
-  S = S * t2 + 1.0f;
-  const bool low = z <= rho;
-  const float u = __fdividef(low ? opr : D + zr, low ? D - zr : omr);
-  const float L = lg2_approx(u) * 0.69314718055994531f;
-  const bool near = fabsf(t) < 0.25f;
-  zn = near ? onepD * 0.5f : z;
-  xd = near ? S : L;
-}
-
-template <class R>
-__device__ __forceinline__ R z_over_x(R z, R rho, R omr, R opr) {
-  R zn, xd;
-  z_over_x_parts<R>(z, rho, omr, opr, zn, xd);
-  return m_div(zn, xd);
+  float S2 = 2.0f / 9.0f;  // 2 S(t^2)
+  S2 = S2 * t2 + 2.0f / 7.0f;
+  S2 = S2 * t2 + 2.0f / 5.0f;
+  S2 = S2 * t2 + 2.0f / 3.0f;
+  S2 = S2 * t2 + 2.0f;
+  const float lg = lg2_approx(D + fabsf(zr));
+  const bool low = zr <= 0.0f;
+  const float x = fmaf(low ? -0.69314718055994531f : 0.69314718055994531f, lg, low ? c.ln_opr : -c.ln_omr);
+  const bool near = fabsf(t) < 0.2f;
+  zn = near ? onepD : z;
+  xd = near ? S2 : x;
 }
 
 // ---------------------------------------------------------------------------
@@ -224,7 +255,9 @@ __device__ __forceinline__ R z_over_x(R z, R rho, R omr, R opr) {
 // ---------------------------------------------------------------------------
 template <class R> struct StaticConst {
   R alpha, beta, rho, nu;
-  R omb, half_omb, c2, c4, nu_over_alpha, br_a, br_b, br_c, omr, opr;
+  R omb, half_omb, c2, c4, nu_over_alpha, br_a, br_b, br_c;
+  R abr_a, abr_b, abr_c;  // alpha br_a, alpha br_b, alpha br_c
+  ZxConst<R> zx;
 };
 
 // params: x[0..3] = alpha, beta, rho, nu (any real type)
@@ -243,23 +276,29 @@ __device__ __forceinline__ StaticConst<R> static_setup(const P* x) {
   s.br_a = s.c2 * s.alpha * s.alpha;
   s.br_b = (R)0.25 * s.rho * s.beta * s.nu * s.alpha;
   s.br_c = m_divc((R)2 - (R)3 * s.rho * s.rho, 24.0) * s.nu * s.nu;
-  s.omr = (R)1 - s.rho;
-  s.opr = (R)1 + s.rho;
+  s.abr_a = s.alpha * s.br_a;
+  s.abr_b = s.alpha * s.br_b;
+  s.abr_c = s.alpha * s.br_c;
+  s.zx = zx_setup<R>(x[2]);
   return s;
 }
 
-// eq. (haganf) with z of eq. (zeta); (K f)^{+-(1-beta)/2} from log2(K f).
+// eq. (haganf) with z of eq. (zeta), fk = (K f)^{(1-beta)/2} = 2^(e) from
+// log2(K f).  The bracket 1 + (br_a/fk^2 + br_b/fk + br_c) T times alpha/fk
+// is written over fk^3, so one power of (K f) serves the whole formula:
+//   sigma = (z/x) [fk^2 (alpha + alpha br_c T) + (alpha br_b fk + alpha br_a) T]
+//           / (fk^3 den).
 template <class R>
 __device__ __forceinline__ R vol_hagan(const StaticConst<R>& s, R lfk, R l2kf, R T) {
-  const R e = s.half_omb * l2kf;
-  const R fk = m_exp2(e), fkinv = m_exp2(-e);
+  const R fk = m_exp2(s.half_omb * l2kf);
   const R L2 = lfk * lfk;
   const R den = (R)1 + L2 * (s.c2 + s.c4 * L2);
-  const R z = s.nu_over_alpha * fk * lfk;
+  const R z = s.nu_over_alpha * lfk * fk;
   R zn, xd;
-  z_over_x_parts<R>(z, s.rho, s.omr, s.opr, zn, xd);
-  const R brk = (R)1 + (s.br_a * fkinv * fkinv + s.br_b * fkinv + s.br_c) * T;
-  return m_div(s.alpha * fkinv * zn * brk, den * xd);
+  z_over_x_parts<R>(z, s.zx, zn, xd);
+  const R fk2 = fk * fk;
+  const R num = fk2 * (s.alpha + s.abr_c * T) + (s.abr_b * fk + s.abr_a) * T;
+  return m_div(zn * num, fk2 * fk * den * xd);
 }
 
 // eq. (sigma-SABR): z = nu (f^{1-b} - K^{1-b}) / (alpha (1-b)); the
@@ -278,7 +317,7 @@ __device__ __forceinline__ R vol_obloj(const StaticConst<R>& s, R lfk, R l2kf, R
   const R den = (R)1 + L2 * (s.c2 + s.c4 * L2);
   const R brk = (R)1 + (s.br_a * fkinv * fkinv + s.br_b * fkinv + s.br_c) * T;
   R zn, xd;
-  z_over_x_parts<R>(z, s.rho, s.omr, s.opr, zn, xd);
+  z_over_x_parts<R>(z, s.zx, zn, xd);
   return m_div(ln * zn * brk, ld * xd * den);
 }
 
