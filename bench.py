@@ -34,10 +34,11 @@ METRIC = "SABR SA cost evals/s (static Hagan surface, 10x21, FP32 bulk)"
 WORKLOAD = ("static Hagan surface: 10 maturities x 21 strikes (each its own smile), 4096 SA chains/smile, "
             "200 levels x 100 proposals, cooling 0.95")
 # Algorithmic work of one Hagan quote evaluation (eq. haganf + the misfit
-# term), by pipe: (K f)^((1-beta)/2) and its reciprocal (two exp2 of a
-# precomputed log), one square root, one logarithm, two divisions, and about
-# 25 FP32 adds/multiplies.
-HAGAN_QUOTE_OPS = {"ex2": 2, "rsq": 1, "lg2": 1, "rcp": 2, "fp32": 25}
+# term), by pipe: (K f)^((1-beta)/2) (one exp2 of a precomputed log; the
+# formula's other powers of K f are its square and cube), one square root,
+# one logarithm, two divisions (t = z/(1 + D) of z/x(z), and the formula's
+# quotient), and about 30 FP32 adds/multiplies.
+HAGAN_QUOTE_OPS = {"ex2": 1, "rsq": 1, "lg2": 1, "rcp": 2, "fp32": 30}
 # One log-Euler path-step: Box-Muller (log, sqrt, sin, cos), the exp of
 # nu-hat, ~12 FP32 operations, and half a Philox4x32-10 block (ten rounds of
 # two 32x32 multiplies, each a low and a high half: 20 integer multiplies).
@@ -651,7 +652,7 @@ def run_ours(args):
         peak_note = ("measured pipe rates (sabr_probe_pipe_rates) x 152 SMs x median SM clock; binding pipe: %s"
                      % pipe)
     else:
-        peak = SMS * sm_mhz * 1e6 / (2 / 32 + 4 / 16) / 1e9
+        peak = SMS * sm_mhz * 1e6 / (1 / 32 + 4 / 16) / 1e9
         peak_note = "nominal SFU rates (ex2 32, others 16 per SM clock) x 152 SMs x median SM clock"
     roofline = {"bound": "alu", "kernel": "sa_level_kernel<float,HAGAN>", "achieved": achieved, "peak": peak,
                 "unit": "Gquote-eval/s", "frac": achieved / peak,
