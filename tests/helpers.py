@@ -1,6 +1,6 @@
 """Shared test helpers: golden-fixture loader and textbook closed forms.
 
-The closed forms here (Black, Bachelier) are the independent references the
+The closed forms here (Black, Bachelier, CEV) are the independent references the
 oracle's special cases are checked against; they are not part of the method.
 """
 import os
@@ -41,6 +41,29 @@ def bachelier_call(f, K, T, sigma_n):
     s = sigma_n * np.sqrt(T)
     d = (f - K) / s
     return (f - K) * norm.cdf(d) + s * norm.pdf(d)
+
+
+def cev_call(f, K, T, alpha, beta):
+    """Call on dF = alpha F^beta dW (SABR with nu = 0), 0 <= beta < 1, F
+    absorbed at 0.  Y = F^(2(1-beta)) / (alpha (1-beta))^2 is a squared
+    Bessel process of dimension delta = (1 - 2 beta)/(1 - beta) (Ito); the
+    process absorbed at 0 is the h-transform, h(y) = y^((2-delta)/2), of the
+    squared Bessel process of dimension 4 - delta, whose Y_T/T is noncentral
+    chi-square (4 - delta degrees, noncentrality Y_0/T).  With
+    (Y_0/Y)^((2-delta)/2) = f/F this gives
+        E[(F_T - K)^+] = f E'[(1 - K/F_T)^+]
+    under the dimension 4 - delta law, evaluated here by one quadrature."""
+    from scipy.integrate import quad
+    from scipy.stats import ncx2
+    b1 = 1.0 - beta
+    c = 1.0 / (alpha * b1) ** 2
+    k = (3.0 - 2.0 * beta) / b1
+    lam = c * f ** (2 * b1) / T
+    uK = c * K ** (2 * b1) / T
+    hi = lam + k + 60.0 * np.sqrt(2 * (k + 2 * lam))
+    inv_f = lambda u: ((u * T / c) ** (-1.0 / (2 * b1)))  # 1 / F at Y = u T
+    tail, _ = quad(lambda u: ncx2.pdf(u, k, lam) * inv_f(u), uK, hi, limit=400, epsabs=1e-14, epsrel=1e-10)
+    return f * (ncx2.sf(uK, k, lam) - K * tail)
 
 
 # Exact law of the Sec. 6.3 cliquet when the forward is a geometric Brownian

@@ -1,7 +1,7 @@
 """Pins of the oracle's random numbers and Monte Carlo pricer (Sec. 4)
 against an independent Philox implementation, distribution tests, and the
-closed forms the SABR SDE reduces to (Black, absorbed Bachelier), plus the
-identities every path must satisfy (put-call, martingale)."""
+closed forms the SABR SDE reduces to (Black, absorbed Bachelier, absorbed
+CEV), plus the identities every path must satisfy (put-call, martingale)."""
 import math
 import os
 
@@ -10,7 +10,7 @@ import pytest
 from scipy import stats
 
 import oracle as O
-from helpers import bachelier_call, black_call
+from helpers import bachelier_call, black_call, cev_call
 
 
 # ---------------------------------------------------------------- Philox
@@ -113,6 +113,33 @@ def test_mc_beta0_nu0_is_absorbed_bachelier():
                            n_paths=1 << 15, steps_per_year=1000, seed=3, n_threads=4)
     ref = bachelier_call(1.0, K, T, a) - bachelier_call(-1.0, K, T, a)
     assert np.all(np.abs(price - ref) <= 4 * se), (price - ref) / se
+
+
+@pytest.mark.parametrize("a,b", [(0.3, 0.5), (0.6, 0.3)])
+def test_mc_nu0_is_absorbed_cev(a, b):
+    # nu = 0, 0 < beta < 1: dF = alpha F^beta dW absorbed at 0 (CEV), whose
+    # call price is a noncentral chi-square expectation (helpers.cev_call,
+    # itself pinned to the absorbed Bachelier at beta = 0 and to Black as
+    # beta -> 1).  Pins the F^(beta - 1) factor of eq. (dis_SABRd) at a beta
+    # where neither limit applies; 250 steps a year leave the log-Euler bias
+    # below the 4-SE band here.
+    T = np.array([0.5, 0.5, 1.0, 1.0, 1.0, 2.0, 2.0])
+    K = np.array([0.8, 1.2, 0.7, 1.0, 1.4, 0.6, 1.5])
+    price, se = O.mc_price(O.HAGAN, [a, b, 0.0, 0.0], 1.0, T, K, n_paths=1 << 16,
+                           steps_per_year=250, seed=5, n_threads=4)
+    ref = np.array([cev_call(1.0, k, t, a, b) for k, t in zip(K, T)])
+    assert np.all(np.abs(price - ref) <= 4 * se), (price - ref) / se
+
+
+def test_cev_reference_limits():
+    # the CEV reference itself: beta = 0 is the absorbed Bachelier call
+    # (reflection), and the error against Black shrinks like 1 - beta
+    for K in (0.5, 1.0, 1.5):
+        ref = bachelier_call(1.0, K, 1.0, 0.4) - bachelier_call(-1.0, K, 1.0, 0.4)
+        assert abs(cev_call(1.0, K, 1.0, 0.4, 0.0) - ref) < 1e-13
+    e1 = cev_call(1.0, 1.1, 1.0, 0.3, 0.99) - black_call(1.0, 1.1, 1.0, 0.3)
+    e2 = cev_call(1.0, 1.1, 1.0, 0.3, 0.999) - black_call(1.0, 1.1, 1.0, 0.3)
+    assert abs(e1) < 1e-4 and 8 < e1 / e2 < 12
 
 
 @pytest.mark.parametrize("model,p", [
