@@ -184,7 +184,7 @@ __device__ __forceinline__ typename CostOf<R>::T group_cost(const R* xp, int n_q
   R acc = (R)0;
   if (MODEL == SABR_HAGAN || MODEL == SABR_OBLOJ) {
     const StaticConst<R> sc = static_setup<R>(xp);
-#pragma unroll 4
+#pragma unroll 3
     for (int q = lane; q < n_quotes; q += G) {
       const QuotePack<R> qp = sq.pack[q];
       const R v = (MODEL == SABR_HAGAN) ? vol_hagan<R>(sc, qp.lfk, qp.l2kf, qp.T)

@@ -333,7 +333,7 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
 // level in .z (level < 0), so that one captured launch serves every step
 // whatever its mix of requests.  Both use this one kernel, so a problem's
 // arithmetic is the same machine code in a plan and in the server.
-// Register budget: the static formulas' quote loop runs four quotes at a
+// Register budget: the static formulas' quote loop runs three quotes at a
 // time (up to 128 registers); the polynomial and dynamic models keep 80.
 template <class R, int MODEL> struct LevelMinBlocks {
   static constexpr int value = sizeof(R) == 8 ? 1 : (MODEL == SABR_HAGAN || MODEL == SABR_OBLOJ ? 2 : 3);
@@ -473,7 +473,7 @@ static int next_pow2(int v) {
   return p;
 }
 
-// About 24 quotes per lane (a lane runs its quote loop four quotes at a
+// About 24 quotes per lane (a lane runs its quote loop three quotes at a
 // time), widened while the batch has fewer than 152 x 256 threads and quotes
 // remain to split; the dynamic models take one lane per maturity (Case I)
 // or per two maturities (Case II).
