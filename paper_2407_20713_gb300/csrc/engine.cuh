@@ -135,40 +135,53 @@ __device__ __forceinline__ DF lanes_sum(float v, int G, unsigned gmask) {
   return s;
 }
 
-// Per-maturity polynomials of a Case II point into coef[3 j ..]: nu1^2,
+// Shared-memory slots per maturity in a chain group's coefficient slice: the
+// polynomial (c0, c1, c2), and for Case II a fourth slot that holds eta2^2
+// until the polynomial is formed.
+template <int MODEL> struct CoefStride {
+  static constexpr int value = MODEL == SABR_DYN_II ? 4 : 3;
+};
+__host__ __device__ constexpr int coef_stride(int model) { return model == SABR_DYN_II ? 4 : 3; }
+
+// Per-maturity polynomials of a Case II point into coef[4 j ..]: nu1^2,
 // nu2^2, eta1 by one lane per maturity; then eta2^2 of each maturity by all
 // G lanes, which split its quadrature nodes and sum them by a fixed-order
-// butterfly (every lane gets the same total).
+// butterfly (every lane gets the same total); then each lane forms the
+// polynomials of the maturities it owns.
 template <class R>
 __device__ __forceinline__ void case2_group_coef(const R* xp, int n_mats, R l2f, const SmemQuotes<R>& sq, R* coef,
                                                  int lane, int G, unsigned gmask) {
-  {
-    const R rho0 = (R)xp[2], nu0 = (R)xp[3], dr = (R)xp[6], dn = (R)xp[7];
-    for (int j = lane; j < n_mats; j += G) {
-      const R T = sq.mT[j];
-      R o3[3];
-      case2_single<R>(rho0, nu0, (R)xp[4] * T, (R)xp[5] * T, dr, dn, (R)xp[8] * T, (R)xp[9] * T, o3);
-      coef[3 * j + 0] = o3[0];
-      coef[3 * j + 1] = o3[1];
-      coef[3 * j + 2] = o3[2];
-    }
-    __syncwarp(gmask);
-    for (int j = 0; j < n_mats; ++j) {
-      const R T = sq.mT[j];
-      const R A = (R)xp[4] * T, B = (R)xp[5] * T, Qr = (R)xp[8] * T, Qn = (R)xp[9] * T;
-      const Eta2Rule<R> rule(A, B);
-      const int nodes = rule.nodes();
-      R part = (R)0;
-      for (int k = lane; k < nodes; k += G) part += rule.node(k, rho0, nu0, A, B, dr, dn, Qr, Qn);
-      for (int off = G >> 1; off > 0; off >>= 1) part += __shfl_xor_sync(gmask, part, off);
-      if (lane == (j & (G - 1))) {
-        const PolyCoef<R> c = dynamic_poly<R>((R)xp[0], (R)xp[1], l2f, T, coef[3 * j + 0], coef[3 * j + 1],
-                                              coef[3 * j + 2], part);
-        coef[3 * j + 0] = c.c0;
-        coef[3 * j + 1] = c.c1;
-        coef[3 * j + 2] = c.c2;
-      }
-    }
+  constexpr int CS = CoefStride<SABR_DYN_II>::value;
+  const R rho0 = (R)xp[2], nu0 = (R)xp[3], dr = (R)xp[6], dn = (R)xp[7];
+  for (int j = lane; j < n_mats; j += G) {
+    const R T = sq.mT[j];
+    R o3[3];
+    case2_single<R>(rho0, nu0, (R)xp[4] * T, (R)xp[5] * T, dr, dn, (R)xp[8] * T, (R)xp[9] * T, o3);
+    coef[CS * j + 0] = o3[0];
+    coef[CS * j + 1] = o3[1];
+    coef[CS * j + 2] = o3[2];
+  }
+  // eta2^2 of every maturity: all lanes share its nodes, a fixed-order
+  // butterfly gives every lane the total, and the lane that owns the
+  // maturity (j mod G) parks it in the slice's fourth slot ...
+  for (int j = 0; j < n_mats; ++j) {
+    const R T = sq.mT[j];
+    const R A = (R)xp[4] * T, B = (R)xp[5] * T, Qr = (R)xp[8] * T, Qn = (R)xp[9] * T;
+    const Eta2Rule<R> rule(A, B);
+    const int nodes = rule.nodes();
+    R part = (R)0;
+    for (int k = lane; k < nodes; k += G) part += rule.node(k, rho0, nu0, A, B, dr, dn, Qr, Qn);
+    for (int off = G >> 1; off > 0; off >>= 1) part += __shfl_xor_sync(gmask, part, off);
+    if (lane == (j & (G - 1))) coef[CS * j + 3] = part;
+  }
+  // ... so that the owners then form their maturities' polynomials side by
+  // side (the slots a lane reads here are the ones it wrote)
+  for (int j = lane; j < n_mats; j += G) {
+    const PolyCoef<R> c = dynamic_poly<R>((R)xp[0], (R)xp[1], l2f, sq.mT[j], coef[CS * j + 0], coef[CS * j + 1],
+                                          coef[CS * j + 2], coef[CS * j + 3]);
+    coef[CS * j + 0] = c.c0;
+    coef[CS * j + 1] = c.c1;
+    coef[CS * j + 2] = c.c2;
   }
 }
 
@@ -204,12 +217,13 @@ __device__ __forceinline__ typename CostOf<R>::T group_cost(const R* xp, int n_q
       acc += r * r;
     }
   } else {
+    constexpr int CS = CoefStride<MODEL>::value;
     if (MODEL == SABR_DYN_I) {
       for (int j = lane; j < n_mats; j += G) {
         const PolyCoef<R> c = dynamic_coef<R, false>(xp, l2f, sq.mT[j]);
-        coef[3 * j + 0] = c.c0;
-        coef[3 * j + 1] = c.c1;
-        coef[3 * j + 2] = c.c2;
+        coef[CS * j + 0] = c.c0;
+        coef[CS * j + 1] = c.c1;
+        coef[CS * j + 2] = c.c2;
       }
     } else {
       case2_group_coef<R>(xp, n_mats, l2f, sq, coef, lane, G, gmask);
@@ -219,9 +233,9 @@ __device__ __forceinline__ typename CostOf<R>::T group_cost(const R* xp, int n_q
       const int j = sq.mat[q];
       const QuotePack<R> qp = sq.pack[q];
       PolyCoef<R> c;
-      c.c0 = coef[3 * j + 0];
-      c.c1 = coef[3 * j + 1];
-      c.c2 = coef[3 * j + 2];
+      c.c0 = coef[CS * j + 0];
+      c.c1 = coef[CS * j + 1];
+      c.c2 = coef[CS * j + 2];
       const R r = resid(vol_poly<R>(c, qp.lfk), qp.w);
       acc += r * r;
     }

@@ -145,8 +145,9 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
   const int g = threadIdx.x / G, lane = threadIdx.x % G;
   // per-maturity polynomial slices exist only for the dynamic models
   const int coef_m = (MODEL == SABR_DYN_I || MODEL == SABR_DYN_II) ? P.n_mats : 0;
-  R* coef = (R*)rest + (size_t)g * 3 * coef_m;
-  double* red_f = (double*)((R*)rest + (size_t)cpb * 3 * coef_m + 16);
+  constexpr int CS = CoefStride<MODEL>::value;
+  R* coef = (R*)rest + (size_t)g * CS * coef_m;
+  double* red_f = (double*)((R*)rest + (size_t)cpb * CS * coef_m + 16);
   red_f = (double*)(((uintptr_t)red_f + 15) & ~(uintptr_t)15);
   R* red_x = (R*)(red_f + cpb);
   __syncthreads();
@@ -501,13 +502,13 @@ size_t level_smem_bytes(int prec, int model, int Q, int M, int cpb) {
   const size_t cm = (model == SABR_DYN_I || model == SABR_DYN_II) ? (size_t)M : 0;
   size_t b = 4 * rs * (size_t)Q + ((size_t)Q + M) * rs + 4 * (size_t)Q;  // pack, l2k, mT, mat
   b = align_up(b, 16);
-  b += (size_t)cpb * 3 * cm * rs + 16 * rs;
+  b += (size_t)cpb * coef_stride(model) * cm * rs + 16 * rs;
   b = align_up(b, 16) + 16;
   b += (size_t)cpb * 8 + (size_t)cpb * kMaxD * rs;
   return align_up(b, 16) + 64;
 }
 
-size_t init_smem_bytes(const HostProblem& h) { return level_smem_bytes(h.prec, SABR_DYN_I, h.n_quotes, h.n_mats, 1); }
+size_t init_smem_bytes(const HostProblem& h) { return level_smem_bytes(h.prec, SABR_DYN_II, h.n_quotes, h.n_mats, 1); }
 
 sabr_status formula_prepare(const sabr_problem& pr, const sabr_bounds& b, const sabr_cooling& c, uint64_t seed,
                             HostProblem& h) {

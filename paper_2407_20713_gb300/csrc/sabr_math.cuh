@@ -40,6 +40,12 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 __device__ __forceinline__ float m_exp2(float x) { return ex2_approx(x); }
+// e^x of the Case II quadrature nodes (x <= 0): in FP32 2^(x log2 e) by the
+// SFU, whose relative error (a few 1e-7 for |x| < 1, growing like
+// |x| 2^-24 from the rounded product) stays far inside the FP32 form's
+// tolerance; in FP64 the library exp.
+__device__ __forceinline__ float m_exp_node(float x) { return ex2_approx(x * 1.4426950408889634f); }
+__device__ __forceinline__ double m_exp_node(double x) { return exp(x); }
 __device__ __forceinline__ double m_exp2(double x) { return exp2(x); }
 __device__ __forceinline__ float m_log(float x) { return logf(x); }
 __device__ __forceinline__ double m_log(double x) { return log(x); }
@@ -519,7 +525,7 @@ __device__ __forceinline__ void case2_single(R rho0, R nu0, R A, R B, R dr, R dn
 template <class R>
 __device__ __forceinline__ R case2_G(R s, R rho0, R nu0, R A, R B, R dr, R dn, R Qr, R Qn) {
   R pAB[3], pB[2], pA[2];
-  const R eA = m_exp(-A * s), eB = m_exp(-B * s);  // e^{-(A+B)s} = eA eB
+  const R eA = m_exp_node(-A * s), eB = m_exp_node(-B * s);  // e^{-(A+B)s} = eA eB
   phi_vec_e<R, 2>((A + B) * s, eA * eB, pAB);
   phi_vec_e<R, 1>(B * s, eB, pB);
   phi_vec_e<R, 1>(A * s, eA, pA);

@@ -142,7 +142,7 @@ static size_t server_smem(int prec, int model, int max_quotes) {
   // models at most 256 maturity slices per block (lanes >= maturities)
   const size_t rs = prec == SABR_FP64 ? 8 : 4;
   size_t b = level_smem_bytes(prec, SABR_HAGAN, max_quotes, kMaxMats, 256);
-  if (model == SABR_DYN_I || model == SABR_DYN_II) b += 256 * 3 * rs + 64;
+  if (model == SABR_DYN_I || model == SABR_DYN_II) b += 256 * coef_stride(model) * rs + 64;
   return b;
 }
 
