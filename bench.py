@@ -90,10 +90,10 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 form")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extra", action="store_true", help="skip the MC, dynamic and serving measurements")
-    ap.add_argument("--case", choices=["full", "small", "mc", "cliquet"], default="full",
+    ap.add_argument("--case", choices=["full", "small", "mc", "cliquet", "dynamic2"], default="full",
                     help="small: 2 smiles x 10 levels, main measurement only; mc: one 2^20-path MC pricing "
-                         "of the MC surface; cliquet: one 2^20-path cliquet (the last three for profiler "
-                         "captures)")
+                         "of the MC surface; cliquet: one 2^20-path cliquet; dynamic2: two runs of three "
+                         "levels of the joint Case II fit (the last four for profiler captures)")
     ap.add_argument("--serve-requests", type=int, default=400)
     return ap.parse_args()
 
@@ -533,6 +533,27 @@ def run_mc_case():
     print(json.dumps({"case": "mc", "ok": True}))
 
 
+def run_dynamic2_case():
+    """Three levels of the joint Case II fit (12 maturities x 21 strikes, 8192
+    chains, FP32) as one plan (profiling)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2407_20713_gb300 as sg
+    from paper_2407_20713_gb300 import workloads
+    w = workloads.dynamic_surface(case=2, feasible=lambda x: _case2_ok(x, float(workloads.DYN_MATURITIES[-1])))
+    mkt = sg.implied_vol(sg.DYN_II, w.truth, 1.0, w.T, w.K, prec=sg.FP64).cpu().numpy() + w.noise
+    pb = sg.CalibrationProblem(model=sg.DYN_II, T=w.T, K=w.K, market=mkt, lo=w.lo, hi=w.hi, prec=sg.FP32,
+                               n_chains=w.n_chains, n_levels=3, chain_len=CHAIN_LEN, seed=3)
+    plan = sg.Plan([pb], use_graph=True)
+    for _ in range(2):
+        plan.run(torch.cuda.current_stream())
+        plan.results()
+    plan.close()
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "dynamic2", "ok": True}))
+
+
 def run_cliquet_case():
     """One sabr_mc_cliquet of the Sec. 6.3 contract at 2^20 paths (profiling)."""
     import torch
@@ -721,5 +742,7 @@ if __name__ == "__main__":
         run_mc_case()
     elif a.case == "cliquet":
         run_cliquet_case()
+    elif a.case == "dynamic2":
+        run_dynamic2_case()
     else:
         run_ours(a)

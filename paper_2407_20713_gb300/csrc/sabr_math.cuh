@@ -247,12 +247,13 @@ __device__ __forceinline__ void z_over_x_parts<float>(float z, const ZxConst<flo
   S2 = S2 * t2 + 2.0f / 5.0f;
   S2 = S2 * t2 + 2.0f / 3.0f;
   S2 = S2 * t2 + 2.0f;
+  // |x| = |lg ln 2 - ln(1 -+ rho)| (the sign of x is that of z, so
+  // z/x = |z|/|x|; the near-branch values are positive)
   const float lg = lg2_approx(D + fabsf(zr));
-  const bool low = zr <= 0.0f;
-  const float x = fmaf(low ? -0.69314718055994531f : 0.69314718055994531f, lg, low ? c.ln_opr : -c.ln_omr);
+  const float ax = fmaf(lg, 0.69314718055994531f, zr > 0.0f ? -c.ln_omr : -c.ln_opr);
   const bool near = fabsf(t) < 0.2f;
-  zn = near ? onepD : z;
-  xd = near ? S2 : x;
+  zn = fabsf(near ? onepD : z);
+  xd = fabsf(near ? S2 : ax);
 }
 
 // ---------------------------------------------------------------------------
