@@ -70,6 +70,8 @@ def lib():
         L.orc_philox4x32_10.restype = None
         L.orc_u01.argtypes = [ctypes.c_uint32]
         L.orc_u01.restype = _D
+        L.orc_sa_uniforms.argtypes = [_PU32, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _PD]
+        L.orc_sa_uniforms.restype = None
         L.orc_box_muller.argtypes = [_D, _D, _PD, _PD]
         L.orc_box_muller.restype = None
         L.orc_mc_grid.argtypes = [_PD, _I64, _D, _PD, _I64]
@@ -184,6 +186,15 @@ def philox(ctr, key):
 
 def u01(w):
     return lib().orc_u01(int(w) & 0xFFFFFFFF)
+
+
+def sa_uniforms(key, chain, level, step, d):
+    """The d + 1 uniforms of SA proposal (chain, level, step): d moves, then
+    the acceptance uniform."""
+    k = (ctypes.c_uint32 * 2)(*[int(x) & 0xFFFFFFFF for x in key])
+    u = (ctypes.c_double * (d + 1))()
+    lib().orc_sa_uniforms(k, int(chain), int(level), int(step), int(d), u)
+    return np.array(u[:])
 
 
 def box_muller(u1, u2):

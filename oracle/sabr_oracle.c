@@ -698,8 +698,8 @@ static double sa_cost(const sa_ctx* c, const double* x, double* scratch) {
  * carry 9 + 9 + 9 unused low bits; the acceptance uniform u[d] is the 23-bit
  * integer whose bits, high to low, are the low 9 bits of word 0, the low 9
  * of word 1 and the low 5 of word 2, mapped like any other 23-bit draw. */
-static void sa_uniforms(const uint32_t key[2], int chain, int level, int step,
-                        int d, double* u) {
+void orc_sa_uniforms(const uint32_t key[2], int chain, int level, int step,
+                     int d, double* u) {
   uint32_t w[4], spare[3] = {0u, 0u, 0u};
   for (int j = 0; j < d; ++j) {
     if ((j & 3) == 0) {
@@ -774,7 +774,7 @@ int orc_sa_calibrate(int model, int cost, double f, int64_t n,
       double* scr = scratch + n * ch;
       double u[11], xp[10];
       for (int st = 0; st < chain_len; ++st) {
-        sa_uniforms(key, ch, lev, st, d, u);
+        orc_sa_uniforms(key, ch, lev, st, d, u);
         int inside = 1;
         for (int i = 0; i < 10; ++i) xp[i] = 0.0;
         for (int i = 0; i < d; ++i) {

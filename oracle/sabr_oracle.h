@@ -92,6 +92,10 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
                        uint32_t out[4]);
 /* 32-bit word -> uniform in (0,1): ((w >> 9) + 0.5) * 2^-23. */
 double orc_u01(uint32_t w);
+/* The d + 1 uniforms of SA proposal (chain, level, step) of a d-parameter
+ * model: u[0..d-1] move the parameters, u[d] decides acceptance. */
+void orc_sa_uniforms(const uint32_t key[2], int chain, int level, int step,
+                     int d, double* u);
 /* Box-Muller: two uniforms -> two independent standard normals. */
 void orc_box_muller(double u1, double u2, double* z1, double* z2);
 

@@ -59,6 +59,29 @@ def test_uniform_map_is_exact_in_single_precision_and_open():
         assert float(np.float32(u)) == u and 0.0 < u < 1.0
 
 
+@pytest.mark.parametrize("d", [4, 6, 10])
+def test_sa_proposal_words(d):
+    # SA proposal (chain, level, step): the moves are words 0..d-1 of the
+    # Philox blocks (chain, level, step, TAG_SA + j/4); the acceptance
+    # uniform is the 23 bits the moves leave unused (low 9, 9, 5 bits of
+    # words 0, 1, 2).  Layout checked word by word, then the acceptance
+    # uniform's law: uniform, and uncorrelated with every move.
+    key = (0x9E3779B9, 77)
+    for chain, level, step in ((0, 0, 0), (4095, 199, 99), (123, 7, 42)):
+        words = []
+        for b in range((d + 3) // 4):
+            words += O.philox([chain, level, step, O.TAG_SA + b], key)
+        u = O.sa_uniforms(key, chain, level, step, d)
+        assert np.array_equal(u[:d], [O.u01(w) for w in words[:d]])
+        bits = ((words[0] & 511) << 14) | ((words[1] & 511) << 5) | (words[2] & 31)
+        assert u[d] == (bits + 0.5) * 2.0 ** -23
+    n = 1 << 14
+    U = np.array([O.sa_uniforms(key, c, 3, s, d) for c in range(n // 64) for s in range(64)])
+    assert stats.kstest(U[:, d], "uniform").pvalue > 1e-4
+    r = np.corrcoef(U.T)[d, :d]
+    assert np.all(np.abs(r) < 4.5 / math.sqrt(n)), r
+
+
 def _stream(n, key=(123, 456)):
     w = []
     for i in range(n):
