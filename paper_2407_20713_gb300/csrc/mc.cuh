@@ -104,15 +104,16 @@ __device__ __forceinline__ void build_steps(const McDev& P, const double* p, Ste
   }
 }
 
-// FP32: SFU forms.  -2 ln u1 lies in (0, 34] for u1 in [2^-24, 1 - 2^-24], so
-// sqrt = s rsqrt(s); the angle 2 pi u2 - pi lies in (-pi, pi), where the SFU
-// sine and cosine keep an absolute error below 2^-21, and
-// (cos, sin)(2 pi u2) = -(cos, sin)(2 pi u2 - pi).
+// FP32: SFU forms.  -2 ln u1 = -2 ln 2 log2 u1 lies in (0, 34] for u1 in
+// [2^-24, 1 - 2^-24], so sqrt = s rsqrt(s); the angle 2 pi u2 - pi lies in
+// (-pi, pi), where the SFU sine and cosine keep an absolute error below
+// 2^-21, and (cos, sin)(2 pi u2) = -(cos, sin)(2 pi u2 - pi).  Every operand
+// is a normal number, so the flush-to-zero forms apply.
 __device__ __forceinline__ void box_muller(float u1, float u2, float& z1, float& z2) {
-  const float s2 = -2.0f * __logf(u1);
-  const float r = s2 * rsqrtf(s2);
-  float s, c;
-  __sincosf(6.28318530717958647692f * u2 - 3.14159265358979323846f, &s, &c);
+  const float s2 = -1.38629436111989061f * lg2_approx(u1);
+  const float r = s2 * rsqrt_approx(s2);
+  const float ang = 6.28318530717958647692f * u2 - 3.14159265358979323846f;
+  const float s = sin_approx(ang), c = cos_approx(ang);
   z1 = -r * c;
   z2 = -r * s;
 }

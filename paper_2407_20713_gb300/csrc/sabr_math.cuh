@@ -40,6 +40,29 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 __device__ __forceinline__ float m_exp2(float x) { return ex2_approx(x); }
+// The other SFU forms used by the FP32 hot loops, flush-to-zero (every
+// operand they see is a normal number, so no denormal fix-up is needed):
+// reciprocal (1 ulp), reciprocal square root, sine and cosine on (-pi, pi).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sin_approx(float x) {
+  float y;
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float cos_approx(float x) {
+  float y;
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 // e^x of the Case II quadrature nodes (x <= 0): in FP32 2^(x log2 e) by the
 // SFU, whose relative error (a few 1e-7 for |x| < 1, growing like
 // |x| 2^-24 from the rounded product) stays far inside the FP32 form's
@@ -59,9 +82,11 @@ __device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
 // Hot-loop division and square root: in FP32 the SFU reciprocal / rsqrt
 // forms (about 2 ulp), in FP64 the IEEE operations.
-__device__ __forceinline__ float m_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float m_div(float a, float b) { return a * rcp_approx(b); }
 __device__ __forceinline__ double m_div(double a, double b) { return a / b; }
-__device__ __forceinline__ float m_sqrt_pos(float x) { return x * rsqrtf(x); }  // x > 0
+__device__ __forceinline__ float m_sqrt_pos(float x) { return x * rsqrt_approx(x); }  // x > 0
+__device__ __forceinline__ float m_rcp(float x) { return rcp_approx(x); }
+__device__ __forceinline__ double m_rcp(double x) { return 1.0 / x; }
 // Division by a constant: FP32 multiplies by the rounded reciprocal (one
 // extra rounding), FP64 divides as written.
 __device__ __forceinline__ float m_divc(float a, double c) { return a * (float)(1.0 / c); }
@@ -232,15 +257,24 @@ template <> __device__ __forceinline__ ZxConst<float> zx_setup<float, double>(do
   c.ln_omr = lg2_approx(c.omr) * 0.69314718055994531f;
   return c;
 }
+// A float rho: 1 -+ rho rounded once in FP32 is the value the FP64 route
+// gives (the exact difference rounded to float), without FP64 instructions.
 template <> __device__ __forceinline__ ZxConst<float> zx_setup<float, float>(float rho) {
-  return zx_setup<float, double>((double)rho);
+  ZxConst<float> c;
+  c.rho = rho;
+  c.omr = 1.0f - rho;
+  c.opr = 1.0f + rho;
+  c.q0 = c.omr * c.opr;
+  c.ln_opr = lg2_approx(c.opr) * 0.69314718055994531f;
+  c.ln_omr = lg2_approx(c.omr) * 0.69314718055994531f;
+  return c;
 }
 template <>
 __device__ __forceinline__ void z_over_x_parts<float>(float z, const ZxConst<float>& c, float& zn, float& xd) {
   const float zr = z - c.rho;
   const float D = m_sqrt_pos(zr * zr + c.q0);
   const float onepD = 1.0f + D;
-  const float t = __fdividef(z, onepD);
+  const float t = z * rcp_approx(onepD);
   const float t2 = t * t;
   float S2 = 2.0f / 9.0f;  // 2 S(t^2)
   S2 = S2 * t2 + 2.0f / 7.0f;
@@ -419,7 +453,7 @@ __device__ __forceinline__ void case1_coeffs(R nu0, R rho0, R a, R b, R T, R out
     g1 = s1;
     g2 = s2;
   } else {
-    const R e = m_exp(-x), ix = (R)1 / x, ix3 = ix * ix * ix;
+    const R e = m_exp(-x), ix = m_rcp(x), ix3 = ix * ix * ix;
     g1 = ((x * x * (R)0.5 - x + (R)1) - e) * ix3;
     g2 = ((R)2 * (e - (R)1) + x * (e + (R)1)) * ix3;
   }
@@ -434,7 +468,7 @@ __device__ __forceinline__ void case1_coeffs(R nu0, R rho0, R a, R b, R T, R out
     g3 = s3;
     g4 = s4;
   } else {
-    const R e = m_exp(-y), iy = (R)1 / y, iy2 = iy * iy;
+    const R e = m_exp(-y), iy = m_rcp(y), iy2 = iy * iy;
     g3 = (e - (R)1 + y) * iy2;
     g4 = (m_exp(-(R)2 * y) - (R)8 * e + ((R)7 + (R)2 * y * (y - (R)3))) * iy2 * iy2;
   }
@@ -470,7 +504,7 @@ __device__ __forceinline__ void phi_vec_e(R x, R e, R* phi) {
       phi[m] = (R)cx_fact(m) * e * S;
     }
   } else {
-    const R ix = (R)1 / x;
+    const R ix = m_rcp(x);
     phi[0] = ((R)1 - e) * ix;
 #pragma unroll
     for (int m = 1; m <= M; ++m) phi[m] = ((R)m * phi[m - 1] - e) * ix;
@@ -502,12 +536,12 @@ __device__ __forceinline__ void case2_single(R rho0, R nu0, R A, R B, R dr, R dn
   const R b0 = nu0, b1 = Qn - (R)2 * nu0, b2 = nu0 - (R)2 * Qn, b3 = Qn;
   const R nu1 = (R)3 * (a0 * f2B[0] + a1 * f2B[1] + a2 * f2B[2] + a3 * f2B[3] + a4 * f2B[4] +
                         (R)2 * dn * (b0 * fB[0] + b1 * fB[1] + b2 * fB[2] + b3 * fB[3]) +
-                        dn * dn / (R)3);
+                        m_divc(dn * dn, 3.0));
   // (1-t) t P = p0 t + (p1 - p0) t^2 + (p2 - p1) t^3 - p2 t^4
   // (1-t) t Rn = nu0 t + (Qn - nu0) t^2 - Qn t^3
   const R nu2 = (R)6 * (p0 * f2B[1] + (p1 - p0) * f2B[2] + (p2 - p1) * f2B[3] - p2 * f2B[4] +
                         (R)2 * dn * (nu0 * fB[1] + (Qn - nu0) * fB[2] - Qn * fB[3]) +
-                        dn * dn / (R)6);
+                        m_divc(dn * dn, 6.0));
   // nu rho = Kp(t) e^{-(A+B)t} + dr Rn e^{-Bt} + dn (rho0 + Qr t) e^{-At} + dn dr
   // Kp = k0 + k1 t + k2 t^2
   const R k0 = nu0 * rho0, k1 = nu0 * Qr + Qn * rho0, k2 = Qn * Qr;
@@ -515,7 +549,7 @@ __device__ __forceinline__ void case2_single(R rho0, R nu0, R A, R B, R dr, R dn
   const R eta1 = (R)2 * (k0 * fAB[0] + (k1 - k0) * fAB[1] + (k2 - k1) * fAB[2] - k2 * fAB[3] +
                          dr * (nu0 * fB[0] + (Qn - nu0) * fB[1] - Qn * fB[2]) +
                          dn * (rho0 * fA[0] + (Qr - rho0) * fA[1] - Qr * fA[2]) +
-                         dn * dr / (R)2);
+                         m_divc(dn * dr, 2.0));
   out3[0] = nu1;
   out3[1] = nu2;
   out3[2] = eta1;
@@ -595,7 +629,7 @@ template <> struct Eta2Rule<float> {
   __device__ Eta2Rule(float A, float B) {
     lam = 0.5f * lg2_approx(1.0f + (A + B)) * 0.69314718055994531f;
     flat = lam < 1e-6f;
-    inv_em = flat ? 0.0f : 1.0f / expm1f(lam);
+    inv_em = flat ? 0.0f : rcp_approx(expm1f(lam));
   }
   __device__ int nodes() const { return kNodes; }
   __device__ float node(int k, float rho0, float nu0, float A, float B, float dr, float dn, float Qr,
