@@ -183,6 +183,13 @@ __device__ __forceinline__ uint32_t sa_accept_word(uint32_t w0, uint32_t w1, uin
 template <class R> __device__ __forceinline__ R u01(uint32_t w) {
   return fma((R)(w >> 9), (R)1.1920928955078125e-07, (R)5.9604644775390625e-08);
 }
+// FP32: the same value without an integer conversion.  The float with bits
+// 0x3F800000 | (w >> 9) is 1 + (w >> 9) 2^-23 exactly, and subtracting
+// 1 - 2^-24 from it is exact (Sterbenz: both lie in [1/2, 2]), leaving
+// (w >> 9) 2^-23 + 2^-24.
+template <> __device__ __forceinline__ float u01<float>(uint32_t w) {
+  return __uint_as_float(0x3F800000u | (w >> 9)) - 0.99999994039535522f;
+}
 
 // ---------------------------------------------------------------------------
 // z / x(z), eq. (equis):  x = ln u,  u = (D + z - rho)/(1 - rho),
