@@ -210,7 +210,15 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
       // words by shuffles; otherwise each lane computes all NB blocks of
       // every step.
       uint32_t wv[4 * NB];
-      if (G >= NB) {
+      if (NB == 1 && G == 1) {
+        // one lane, one block: no exchange
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)chain, (uint32_t)level, (uint32_t)st, kTagSA),
+                                      P.key0, P.key1);
+        wv[0] = w.x;
+        wv[1] = w.y;
+        wv[2] = w.z;
+        wv[3] = w.w;
+      } else if (G >= NB) {
         const int s_in = s_ctr;
         s_ctr = s_ctr + 1 == S ? 0 : s_ctr + 1;
         if (s_in == 0) {

@@ -498,7 +498,31 @@ __device__ __forceinline__ void case1_coeffs(R nu0, R rho0, R a, R b, R T, R out
 // phi_0..phi_M at x >= 0, given e = e^{-x}.
 template <class R, int M>
 __device__ __forceinline__ void phi_vec_e(R x, R e, R* phi) {
-  if (x < (R)Tr<R>::kSeriesMax) {
+  if constexpr (sizeof(R) == 4) {
+    // FP32: both forms, then a select per phi_m -- the lanes of a chain hold
+    // different quadrature nodes, and a branch on x would run both forms
+    // one after the other whenever they disagree
+    constexpr int N = Tr<R>::kSeries;
+    R S = (R)(1.0 / cx_fact(M + N + 1));
+#pragma unroll
+    for (int n = N - 1; n >= 0; --n) S = S * x + (R)(1.0 / cx_fact(M + n + 1));
+    R ser[M + 1];
+    ser[M] = (R)cx_fact(M) * e * S;
+#pragma unroll
+    for (int m = M - 1; m >= 0; --m) {
+      S = (R)(1.0 / cx_fact(m + 1)) + x * S;
+      ser[m] = (R)cx_fact(m) * e * S;
+    }
+    const bool use_series = x < (R)Tr<R>::kSeriesMax;
+    const R ix = m_rcp(x);
+    R rec = ((R)1 - e) * ix;
+    phi[0] = use_series ? ser[0] : rec;
+#pragma unroll
+    for (int m = 1; m <= M; ++m) {
+      rec = ((R)m * rec - e) * ix;
+      phi[m] = use_series ? ser[m] : rec;
+    }
+  } else if (x < (R)Tr<R>::kSeriesMax) {
     constexpr int N = Tr<R>::kSeries;
     // S_M(x) = sum_{n=0..N} x^n/(M+n+1)! by Horner's rule, one FMA a term
     R S = (R)(1.0 / cx_fact(M + N + 1));
