@@ -201,6 +201,9 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
     constexpr int NB = sa_philox_blocks(D);  // Philox blocks per step
     const int S = G >= NB ? G / NB : 1;  // steps per batch of Philox blocks
     int s_ctr = 0;                         // st mod S
+    uint4 wnext = make_uint4(0u, 0u, 0u, 0u);
+    if (NB == 1 && G == 1)
+      wnext = philox4x32_10(make_uint4((uint32_t)chain, (uint32_t)level, 0u, kTagSA), P.key0, P.key1);
     for (int st = 0; st < P.chain_len; ++st) {
       // D Philox words of blocks 0, 1, ... with counter (chain, level, step,
       // tag + block): D move uniforms and, from their unused low bits, the
@@ -211,9 +214,12 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
       // every step.
       uint32_t wv[4 * NB];
       if (NB == 1 && G == 1) {
-        // one lane, one block: no exchange
-        const uint4 w = philox4x32_10(make_uint4((uint32_t)chain, (uint32_t)level, (uint32_t)st, kTagSA),
-                                      P.key0, P.key1);
+        // one lane, one block: no exchange; the block of the next step is
+        // formed here, off the critical path of this one (its counter does
+        // not depend on this step's outcome)
+        const uint4 w = wnext;
+        wnext = philox4x32_10(make_uint4((uint32_t)chain, (uint32_t)level, (uint32_t)(st + 1), kTagSA), P.key0,
+                              P.key1);
         wv[0] = w.x;
         wv[1] = w.y;
         wv[2] = w.z;
