@@ -234,7 +234,10 @@ typedef struct {
  * chains start from x0; each runs chain_len Metropolis steps per temperature
  * level; the lowest final state restarts every chain at the next level.
  * Proposal uniforms of chain c at (level k, step j) come from Philox4x32-10
- * with key = seed and counter (c, k, j, 0x53410000 + block).  Out-of-box
+ * with key = seed and counter (c, k, j, 0x53410000 + block): the top 23 bits
+ * of words 0 .. d-1 move the d parameters, and the acceptance uniform is the
+ * 23 bits those words leave unused (low 9, 9 and 5 bits of words 0, 1, 2),
+ * so a static model draws one block per proposal.  Out-of-box
  * (and, for DYN_II, infeasible) proposals are rejected without a cost
  * evaluation.  Blocking: returns when *out is filled.  Results depend only on
  * (problem, bounds, cooling, seed) and G, the lanes that share a chain's
