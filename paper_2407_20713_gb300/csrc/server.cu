@@ -139,10 +139,12 @@ namespace sabr {
 
 static size_t server_smem(int prec, int model, int max_quotes) {
   // worst case over lane counts: 256 chains per block, and for the dynamic
-  // models at most 256 maturity slices per block (lanes >= maturities)
+  // models at most 512 maturity slices per block (G lanes per chain hold
+  // its M maturities, with G >= M/2 rounded to a power of two, and G = 1
+  // only for M <= 2)
   const size_t rs = prec == SABR_FP64 ? 8 : 4;
   size_t b = level_smem_bytes(prec, SABR_HAGAN, max_quotes, kMaxMats, 256);
-  if (model == SABR_DYN_I || model == SABR_DYN_II) b += 256 * coef_stride(model) * rs + 64;
+  if (model == SABR_DYN_I || model == SABR_DYN_II) b += 512 * coef_stride(model) * rs + 64;
   return b;
 }
 

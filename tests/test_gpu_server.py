@@ -113,6 +113,27 @@ def test_admission_respects_the_device_pool():
     assert 0 < peak <= 4 << 20
 
 
+@pytest.mark.parametrize("model", [sg.DYN_I, sg.DYN_II])
+def test_dynamic_request_at_the_shared_memory_worst_case(model):
+    # two maturities and few quotes give one lane per chain, and enough chains
+    # keep it from widening: 256 chains of two maturity slices each per
+    # block, with max_quotes leaving no slack in the quote staging
+    T = np.repeat([0.5, 2.0], 21)
+    K = np.tile(np.linspace(0.6, 1.4, 21), 2)
+    if model == sg.DYN_I:
+        truth, lo, hi = [0.25, 0.8, -0.4, 0.6, 0.5, 0.8], workloads.DYN1_LO, workloads.DYN1_HI
+    else:
+        truth, lo, hi = [0.25, 0.8, -0.4, 0.6, 0.5, 0.8, 0.05, 0.1, 0.1, 0.05], workloads.DYN2_LO, workloads.DYN2_HI
+    mkt = O.implied_vol(model, truth, 1.0, T, K)
+    pb = sg.CalibrationProblem(model=model, T=T, K=K, market=mkt, lo=lo, hi=hi, n_chains=152 * 256, n_levels=3,
+                               chain_len=8, seed=5)
+    srv = sg.Server(device_bytes=256 << 20, max_quotes=T.size)
+    r = srv.wait(srv.submit(pb), timeout_ms=60000)
+    srv.close()
+    alone = sg.calibrate(pb)
+    assert r.status == 0 and r.misfit_fp64 == alone.misfit_fp64 and np.array_equal(r.params, alone.params)
+
+
 def test_host_side_limits_and_status_codes():
     srv = sg.Server(device_bytes=64 << 20, max_queue=2, max_active=1)
     t1 = srv.submit(formula_request(6, n_chains=16384, n_levels=4000, chain_len=200))
