@@ -49,25 +49,52 @@ SMS = 152
 LEVEL_KERNEL_SOURCES = ["sa.cu", "engine.cuh", "sabr_math.cuh"]
 
 
-def profiled_traffic(profile, sources):
-    """DRAM bytes (read + write) per launch from a committed ncu summary under
-    profiles/, or None when the kernel's sources have changed since that
-    capture (the summary records their SHA-256)."""
+def _current_profile(profile, sources):
+    """Text of a committed ncu summary under profiles/, or None when the
+    kernel's sources have changed since that capture (the summary records
+    their SHA-256)."""
     import hashlib
     import re
     try:
         text = open(os.path.join(ROOT, "profiles", profile)).read()
     except OSError:
         return None
-    t = re.search(r"^traffic_bytes_per_launch: (\d+)", text, re.M)
     h = re.search(r"^source_sha256[^:]*: ([0-9a-f]{64})", text, re.M)
-    if not t or not h:
+    if not h:
         return None
     d = hashlib.sha256()
     for f in sources:
         with open(os.path.join(ROOT, "paper_2407_20713_gb300", "csrc", f), "rb") as fh:
             d.update(fh.read())
-    return int(t.group(1)) if d.hexdigest() == h.group(1) else None
+    return text if d.hexdigest() == h.group(1) else None
+
+
+def profiled_traffic(profile, sources):
+    """DRAM bytes (read + write) per launch from a committed ncu summary, or
+    None when the kernel has changed since the capture."""
+    import re
+    text = _current_profile(profile, sources)
+    t = re.search(r"^traffic_bytes_per_launch: (\d+)", text, re.M) if text else None
+    return int(t.group(1)) if t else None
+
+
+def profiled_thread_instructions(profile, sources):
+    """Thread instructions per launch (warp instructions x active lanes per
+    warp instruction) from a committed ncu summary, or None when the kernel
+    has changed since the capture."""
+    import re
+    text = _current_profile(profile, sources)
+    if not text:
+        return None
+    w = re.search(r"`smsp__inst_executed\.sum`\) \| ([0-9.]+)", text)
+    lanes = re.search(r"`smsp__thread_inst_executed_per_inst_executed\.ratio`\) \| ([0-9.]+)", text)
+    return float(w.group(1)) * float(lanes.group(1)) if w and lanes else None
+
+
+def issue_bound(thread_instr_per_unit, sm_mhz):
+    """Units per second if every issue slot of the GPU (4 schedulers x 32
+    lanes per SM clock) carried one of the unit's instructions."""
+    return SMS * 4 * 32 * sm_mhz * 1e6 / thread_instr_per_unit
 
 
 def pipe_bound(ops, rates, sm_mhz):
@@ -680,6 +707,14 @@ def run_ours(args):
                 "traffic": profiled_traffic("sa_level_kernel_hagan_static_surface.md", LEVEL_KERNEL_SOURCES),
                 "launch_ms": lvl_ms, "quote_evals_per_launch": quote_evals_per_launch, "peak_from": peak_note,
                 "pipe_rates_per_sm_clk": rates}
+    ti = profiled_thread_instructions("sa_level_kernel_hagan_static_surface.md", LEVEL_KERNEL_SOURCES)
+    if ti:
+        # the ceiling the kernel actually meets: issue slots, at the
+        # instructions per quote evaluation of the committed capture
+        per_unit = ti / quote_evals_per_launch
+        ib = issue_bound(per_unit, sm_mhz) / 1e9
+        roofline["issue_bound"] = {"thread_instructions_per_unit": per_unit, "peak": ib, "frac": achieved / ib,
+                                   "from": "ncu warp instructions x active lanes of the committed capture"}
 
     line = {"metric": METRIC, "value": value,
             "unit": "cost-evals/s", "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),

@@ -53,3 +53,27 @@ def test_aggregate_single_process():
     import bench
     res = bench.aggregate(2.0, 10.0, 3.0, None)
     assert res == {"time_s": 2.0, "units": 10.0, "value": 5.0, "e2e": 3.0}
+
+
+def test_profile_figures_are_read_only_while_the_kernel_is_unchanged(tmp_path, monkeypatch):
+    # bench.py takes DRAM traffic and instructions per launch from the
+    # committed ncu summary, and drops both once a source of the kernel no
+    # longer matches the hash the summary records
+    sys.path.insert(0, ROOT)
+    import bench
+    prof = ("| warp instructions (`smsp__inst_executed.sum`) | 1000.0 inst |\n"
+            "| active lanes per warp instruction (`smsp__thread_inst_executed_per_inst_executed.ratio`) | 25.0  |\n"
+            "traffic_bytes_per_launch: 4096\nsource_sha256 (k.cu): %s\n")
+    import hashlib
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "paper_2407_20713_gb300" / "csrc").mkdir(parents=True)
+    src = tmp_path / "paper_2407_20713_gb300" / "csrc" / "k.cu"
+    src.write_bytes(b"kernel v1")
+    (tmp_path / "profiles" / "k.md").write_text(prof % hashlib.sha256(b"kernel v1").hexdigest())
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.profiled_traffic("k.md", ["k.cu"]) == 4096
+    assert bench.profiled_thread_instructions("k.md", ["k.cu"]) == 25000.0
+    assert abs(bench.issue_bound(50.0, 2000.0) - 152 * 128 * 2e9 / 50.0) < 1.0
+    src.write_bytes(b"kernel v2")
+    assert bench.profiled_traffic("k.md", ["k.cu"]) is None
+    assert bench.profiled_thread_instructions("k.md", ["k.cu"]) is None
