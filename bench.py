@@ -295,6 +295,14 @@ def measure_mc(sg, torch, stream, rates, sm_mhz):
                                                        ["mc.cu", "mc.cuh", "sabr_math.cuh"]),
                            "traffic_note": "DRAM bytes per launch from the 2^20-path capture: the tables, "
                                            "independent of the path count"}
+        ti = profiled_thread_instructions("mc_paths_kernel_mc_surface.md", ["mc.cu", "mc.cuh", "sabr_math.cuh"])
+        if ti:
+            per_unit = ti / ((1 << 20) * steps)   # the capture prices 2^20 paths on the same grid
+            ib = issue_bound(per_unit, sm_mhz)
+            res["roofline"]["issue_bound"] = {"thread_instructions_per_unit": per_unit, "peak": ib,
+                                              "frac": res["value"] / ib,
+                                              "from": "ncu warp instructions x active lanes of the committed "
+                                                      "2^20-path capture"}
     return res
 
 
@@ -328,6 +336,15 @@ def measure_cliquet(sg, torch, stream, rates, sm_mhz):
                            "frac": res["value"] / peak,
                            "traffic": profiled_traffic("cliquet_kernel_dsabr1_2p20.md",
                                                        ["cliquet.cu", "mc.cuh", "sabr_math.cuh"])}
+        ti = profiled_thread_instructions("cliquet_kernel_dsabr1_2p20.md", ["cliquet.cu", "mc.cuh", "sabr_math.cuh"])
+        if ti:
+            per_unit = ti / (n_paths * steps)   # the capture is this workload
+            ib = issue_bound(per_unit, sm_mhz)
+            res["roofline"]["issue_bound"] = {"thread_instructions_per_unit": per_unit, "peak": ib,
+                                              "frac": res["value"] / ib,
+                                              "from": "ncu warp instructions x active lanes of the committed "
+                                                      "capture (the cliquet kernel alone; the value includes "
+                                                      "the call's table upload and reduction)"}
     return res
 
 
