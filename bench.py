@@ -117,10 +117,10 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 form")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extra", action="store_true", help="skip the MC, dynamic and serving measurements")
-    ap.add_argument("--case", choices=["full", "small", "mc", "cliquet", "dynamic2"], default="full",
+    ap.add_argument("--case", choices=["full", "small", "mc", "cliquet", "dynamic1", "dynamic2"], default="full",
                     help="small: 2 smiles x 10 levels, main measurement only; mc: one 2^20-path MC pricing "
-                         "of the MC surface; cliquet: one 2^20-path cliquet; dynamic2: two runs of three "
-                         "levels of the joint Case II fit (the last four for profiler captures)")
+                         "of the MC surface; cliquet: one 2^20-path cliquet; dynamic1 / dynamic2: two runs of "
+                         "three levels of the joint Case I / Case II fit (the last five for profiler captures)")
     ap.add_argument("--serve-requests", type=int, default=400)
     return ap.parse_args()
 
@@ -577,17 +577,18 @@ def run_mc_case():
     print(json.dumps({"case": "mc", "ok": True}))
 
 
-def run_dynamic2_case():
-    """Three levels of the joint Case II fit (12 maturities x 21 strikes, 8192
-    chains, FP32) as one plan (profiling)."""
+def run_dynamic_case(case):
+    """Three levels of the joint Case I or Case II fit (12 maturities x 21
+    strikes, 8192 chains, FP32) as one plan, run twice (profiling)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     import paper_2407_20713_gb300 as sg
     from paper_2407_20713_gb300 import workloads
-    w = workloads.dynamic_surface(case=2, feasible=lambda x: _case2_ok(x, float(workloads.DYN_MATURITIES[-1])))
-    mkt = sg.implied_vol(sg.DYN_II, w.truth, 1.0, w.T, w.K, prec=sg.FP64).cpu().numpy() + w.noise
-    pb = sg.CalibrationProblem(model=sg.DYN_II, T=w.T, K=w.K, market=mkt, lo=w.lo, hi=w.hi, prec=sg.FP32,
+    model = sg.DYN_I if case == 1 else sg.DYN_II
+    w = workloads.dynamic_surface(case=case, feasible=lambda x: _case2_ok(x, float(workloads.DYN_MATURITIES[-1])))
+    mkt = sg.implied_vol(model, w.truth, 1.0, w.T, w.K, prec=sg.FP64).cpu().numpy() + w.noise
+    pb = sg.CalibrationProblem(model=model, T=w.T, K=w.K, market=mkt, lo=w.lo, hi=w.hi, prec=sg.FP32,
                                n_chains=w.n_chains, n_levels=3, chain_len=CHAIN_LEN, seed=3)
     plan = sg.Plan([pb], use_graph=True)
     for _ in range(2):
@@ -595,7 +596,7 @@ def run_dynamic2_case():
         plan.results()
     plan.close()
     torch.cuda.synchronize()
-    print(json.dumps({"case": "dynamic2", "ok": True}))
+    print(json.dumps({"case": "dynamic%d" % case, "ok": True}))
 
 
 def run_cliquet_case():
@@ -794,7 +795,7 @@ if __name__ == "__main__":
         run_mc_case()
     elif a.case == "cliquet":
         run_cliquet_case()
-    elif a.case == "dynamic2":
-        run_dynamic2_case()
+    elif a.case in ("dynamic1", "dynamic2"):
+        run_dynamic_case(int(a.case[-1]))
     else:
         run_ours(a)
