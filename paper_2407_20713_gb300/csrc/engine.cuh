@@ -62,12 +62,19 @@ struct ProblemDev {
 template <class R> struct __align__(16) QuotePack {
   R lfk, l2kf, T, w;
 };
+// The dynamic models read neither log2(K f) nor T per quote (their quotes
+// use the polynomial of their maturity), so their packs carry the quote's
+// maturity index, as integer bits, in the l2kf slot: one load per quote
+// fetches everything its evaluation needs but the polynomial.
+__device__ __forceinline__ float mat_in_slot(int j, float) { return __int_as_float(j); }
+__device__ __forceinline__ double mat_in_slot(int j, double) { return __longlong_as_double((long long)j); }
+__device__ __forceinline__ int mat_of_slot(float v) { return __float_as_int(v); }
+__device__ __forceinline__ int mat_of_slot(double v) { return (int)__double_as_longlong(v); }
 
 // Quote tables of one problem staged in shared memory.
 template <class R> struct SmemQuotes {
   const QuotePack<R>* pack;  // per quote
   const R* l2k;              // per quote: log2 K (Oblój)
-  const int* mat;            // per quote: maturity index
   const R* mT;               // per maturity: T
 };
 
@@ -136,12 +143,23 @@ __device__ __forceinline__ DF lanes_sum(float v, int G, unsigned gmask) {
 }
 
 // Shared-memory slots per maturity in a chain group's coefficient slice: the
-// polynomial (c0, c1, c2), and for Case II a fourth slot that holds eta2^2
-// until the polynomial is formed.
+// polynomial (c0, c1, c2), and a fourth slot (for Case II it holds eta2^2
+// until the polynomial is formed) that aligns each polynomial to 16 bytes.
 template <int MODEL> struct CoefStride {
-  static constexpr int value = MODEL == SABR_DYN_II ? 4 : 3;
+  static constexpr int value = 4;
 };
-__host__ __device__ constexpr int coef_stride(int model) { return model == SABR_DYN_II ? 4 : 3; }
+__host__ __device__ constexpr int coef_stride(int) { return 4; }
+
+// The polynomial of maturity j from a coefficient slice: one 16-byte load
+// in FP32 (the slice is 16-byte aligned and its stride is 4), two in FP64.
+__device__ __forceinline__ PolyCoef<float> load_poly(const float* coef, int j) {
+  const float4 v = *reinterpret_cast<const float4*>(coef + 4 * j);
+  return PolyCoef<float>{v.x, v.y, v.z};
+}
+__device__ __forceinline__ PolyCoef<double> load_poly(const double* coef, int j) {
+  const double2 v = *reinterpret_cast<const double2*>(coef + 4 * j);
+  return PolyCoef<double>{v.x, v.y, coef[4 * j + 2]};
+}
 
 // Per-maturity polynomials of a Case II point into coef[4 j ..]: nu1^2,
 // nu2^2, eta1 by one lane per maturity; then eta2^2 of each maturity by all
@@ -230,12 +248,8 @@ __device__ __forceinline__ typename CostOf<R>::T group_cost(const R* xp, int n_q
     }
     __syncwarp(gmask);
     for (int q = lane; q < n_quotes; q += G) {
-      const int j = sq.mat[q];
       const QuotePack<R> qp = sq.pack[q];
-      PolyCoef<R> c;
-      c.c0 = coef[CS * j + 0];
-      c.c1 = coef[CS * j + 1];
-      c.c2 = coef[CS * j + 2];
+      const PolyCoef<R> c = load_poly(coef, mat_of_slot(qp.l2kf));
       const R r = resid(vol_poly<R>(c, qp.lfk), qp.w);
       acc += r * r;
     }

@@ -34,21 +34,20 @@ __device__ __forceinline__ SmemQuotes<R> stage_quotes(const ProblemDev& P, unsig
   QuotePack<R>* pack = (QuotePack<R>*)base;  // base is 16-byte aligned
   R* l2k = (R*)(pack + Q);
   R* mT = l2k + Q;
-  int* mat = (int*)(mT + M);
+  const bool dyn = P.model == SABR_DYN_I || P.model == SABR_DYN_II;
   for (int i = tid; i < Q; i += nthreads) {
     QuotePack<R> qp;
     qp.lfk = ((const R*)P.q_lfk)[i];
-    qp.l2kf = ((const R*)P.q_l2kf)[i];
+    qp.l2kf = dyn ? mat_in_slot(P.q_mat[i], R{}) : ((const R*)P.q_l2kf)[i];
     qp.T = ((const R*)P.q_T)[i];
     qp.w = ((const R*)P.q_w)[i];
     pack[i] = qp;
     l2k[i] = ((const R*)P.q_l2k)[i];
-    mat[i] = P.q_mat[i];
   }
   for (int j = tid; j < M; j += nthreads) mT[j] = ((const R*)P.m_T)[j];
-  unsigned char* e = (unsigned char*)(mat + Q);
+  unsigned char* e = (unsigned char*)(mT + M);
   *end = (unsigned char*)(((uintptr_t)e + 15) & ~(uintptr_t)15);
-  SmemQuotes<R> sq{pack, l2k, mat, mT};
+  SmemQuotes<R> sq{pack, l2k, mT};
   return sq;
 }
 
@@ -517,7 +516,7 @@ int choose_lanes(int n_quotes, int n_mats, int model, long long batch_chains) {
 size_t level_smem_bytes(int prec, int model, int Q, int M, int cpb) {
   const size_t rs = prec == SABR_FP64 ? 8 : 4;
   const size_t cm = (model == SABR_DYN_I || model == SABR_DYN_II) ? (size_t)M : 0;
-  size_t b = 4 * rs * (size_t)Q + ((size_t)Q + M) * rs + 4 * (size_t)Q;  // pack, l2k, mT, mat
+  size_t b = 4 * rs * (size_t)Q + ((size_t)Q + M) * rs;  // pack, l2k, mT
   b = align_up(b, 16);
   b += (size_t)cpb * coef_stride(model) * cm * rs + 16 * rs;
   b = align_up(b, 16) + 16;
