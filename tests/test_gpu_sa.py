@@ -263,6 +263,9 @@ def test_maximum_quote_and_maturity_counts(prec):
         np.testing.assert_allclose(g.params, o["params"], rtol=1e-10)
     o_fit = O.misfit(O.implied_vol(O.DYN_I, g.params, 1.0, T, K), m)
     assert g.misfit_fp64 == pytest.approx(o_fit, rel=1e-7)
+    # the in-loop cost of the returned point (every quote reading its own
+    # maturity's polynomial, 64 of them) agrees with the FP64 re-score
+    assert abs(g.misfit - g.misfit_fp64) <= 2e-3 * g.misfit_fp64
     # one quote more is refused
     with pytest.raises(sg.SabrError):
         sg.calibrate(sg.CalibrationProblem(model=sg.DYN_I, T=np.append(T, 1.0), K=np.append(K, 1.0),
