@@ -475,10 +475,14 @@ static void mc_start(const double* p, double f, mc_state* s) {
 }
 
 /* Step i of path `path` (from s->t to grid[i]) of the log-Euler scheme,
- * eq. (dis_SABRd), with left-point nu(t_i), rho(t_i) and the OLD alpha_i in
- * nu-hat.  The normals of steps 2m and 2m+1 come from Philox block
- * (path, m, 0, tag) by Box-Muller.  Absorption (a reading; the paper is
- * silent): once F < 1e-12 f the path is frozen at F = 0. */
+ * eq. (dis_SABRd), with the OLD alpha_i in nu-hat.  The time-dependent
+ * nu(t), rho(t) of the step are taken at its right end, grid[i] (a reading:
+ * the equation prints nu(t_i), but the paper's DSabr_II results of Sec. 6.2
+ * -- its EUR/USD prices, and EURO STOXX 50 parameters with rho(0) < -1 --
+ * are those of the scheme whose first step uses t_1, not t_0).  The normals
+ * of steps 2m and 2m+1 come from Philox block (path, m, 0, tag) by
+ * Box-Muller.  Absorption (a reading; the paper is silent): once
+ * F < 1e-12 f the path is frozen at F = 0. */
 static void mc_step(int model, const double* p, double absorb_at, const double* grid, int64_t i,
                     uint32_t path, const uint32_t key[2], mc_state* s) {
   int dyn = (model == ORC_DYN_I) ? 1 : (model == ORC_DYN_II ? 2 : 0);
@@ -491,8 +495,8 @@ static void mc_step(int model, const double* p, double absorb_at, const double* 
   uint32_t wa = (i & 1) ? s->w[2] : s->w[0], wb = (i & 1) ? s->w[3] : s->w[1];
   double z1, z2;
   orc_box_muller(orc_u01(wa), orc_u01(wb), &z1, &z2);
-  double nu = dyn ? orc_nu_t(dyn, p, s->t) : p[3];
-  double rho = dyn ? orc_rho_t(dyn, p, s->t) : p[2];
+  double nu = dyn ? orc_nu_t(dyn, p, grid[i]) : p[3];
+  double rho = dyn ? orc_rho_t(dyn, p, grid[i]) : p[2];
   double sh = sqrt(h);
   if (!s->absorbed) {
     double nuhat = s->alpha * pow(s->F, beta - 1.0);

@@ -182,14 +182,14 @@ sabr_status mc_prepare(int model, double fwd, const double* T, const double* K, 
     const double Tm = h.mats[m];
     while ((double)k / spy < Tm - 1e-10) {
       const double t = (double)k / spy;
-      h.step_t.push_back(prev);
+      h.step_t.push_back(t);
       h.step_h.push_back(t - prev);
       h.step_mat.push_back(-1);
       prev = t;
       ++k;
       if ((int64_t)h.step_t.size() > kMaxMcSteps) return fail(SABR_EINVAL, "more than 8192 time steps");
     }
-    h.step_t.push_back(prev);
+    h.step_t.push_back(Tm);
     h.step_h.push_back(Tm - prev);
     h.step_mat.push_back((int)m);
     prev = Tm;

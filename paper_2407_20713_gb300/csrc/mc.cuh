@@ -20,7 +20,8 @@ struct McDev {
   int64_t n_paths;
   double fwd, log_absorb;  // ln(1e-12 f)
   uint32_t key0, key1;
-  const double* step_t;    // [n_steps] left end t_i of step i
+  const double* step_t;    // [n_steps] right end t_{i+1} of step i, where
+                           // its nu(t), rho(t) are taken
   const double* step_h;    // [n_steps] length of step i
   const int* step_mat;     // [n_steps] maturity reached at the end of step i, or -1
   const int* mat_q0;       // [n_mats] first quote of each maturity

@@ -8,7 +8,7 @@ import pytest
 
 import oracle as O
 import paper_2407_20713_gb300 as sg
-from helpers import black_call, cev_call
+from helpers import Golden, black_call, cev_call
 
 pytestmark = pytest.mark.gpu
 
@@ -101,6 +101,22 @@ def test_mc_log_euler_bias_against_cev(a, b):
     d1000, se1000 = bias[1000]
     assert np.all(np.abs(d1000) <= 4 * se1000 + 0.25 * np.max(np.abs(d25)))
     assert np.max(np.abs(d1000)) <= np.max(np.abs(d25)) + 4 * np.max(se1000)
+
+
+@pytest.mark.parametrize("prec", [sg.FP32, sg.FP64])
+def test_mc_reproduces_the_papers_dsabr2_eurusd_prices(prec):
+    # the paper's DSabr_II EUR/USD prices (Sec. 6.2.2) at its calibrated
+    # parameters, through the C-ABI at 2^20 paths (the paper's count)
+    g = Golden("dsabr2_eurusd.txt")
+    p, S0 = g.floats("params"), g.floats("spot")[0]
+    for T in sorted(set(g.rows[:, 0])):
+        rows = g.rows[g.rows[:, 0] == T]
+        r, y, K, V = rows[0, 1], rows[0, 2], rows[:, 3], rows[:, 4]
+        F = S0 * np.exp((r - y) * T)
+        got, se = sg.mc_price(sg.DYN_II, p, F, np.full(K.size, T), K, discount=np.full(K.size, np.exp(-r * T)),
+                              n_paths=1 << 20, steps_per_year=250, seed=9, prec=prec)
+        got, se = got.cpu().numpy(), se.cpu().numpy()
+        assert np.all(np.abs(got - V) <= 4 * se + 0.005 * V), (T, (got - V) / V)
 
 
 def test_mc_is_deterministic_and_validates():
