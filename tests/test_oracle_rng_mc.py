@@ -175,6 +175,21 @@ def test_mc_reproduces_the_papers_dsabr2_eurusd_prices():
         assert np.all(np.abs(price - V) <= 4 * se + 0.005 * V), (T, (price - V) / V)
 
 
+@pytest.mark.parametrize("name,model", [("DYN_I", O.DYN_I), ("DYN_II", O.DYN_II)])
+def test_mc_reproduces_the_papers_european_call_table(name, model):
+    # Sec. 4's table of European call prices (double precision, 2^20 paths,
+    # 123 steps of 1/250) at the section's DSabr_I and DSabr_II parameters;
+    # the bound, 5 SE at 2^19 paths, covers the paper's own Monte Carlo noise
+    g = Golden("table1_european_call.txt")
+    S0, K, T = g.floats("spot")[0], g.floats("strike")[0], g.floats("maturity")[0]
+    r, y = g.floats("rates")
+    n_steps = int(g.floats("steps")[0])
+    V, *p = g.floats(name)
+    price, se = O.mc_price(model, p, S0 * math.exp((r - y) * T), [n_steps / 250.0], [K],
+                           disc=[math.exp(-r * T)], n_paths=1 << 19, steps_per_year=250, seed=5, n_threads=8)
+    assert abs(price[0] - V) <= 5 * se[0], (price[0], V, se[0])
+
+
 def test_cev_reference_limits():
     # the CEV reference itself: beta = 0 is the absorbed Bachelier call
     # (reflection), and the error against Black shrinks like 1 - beta
