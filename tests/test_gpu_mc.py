@@ -119,6 +119,24 @@ def test_mc_reproduces_the_papers_dsabr2_eurusd_prices(prec):
         assert np.all(np.abs(got - V) <= 4 * se + 0.005 * V), (T, (got - V) / V)
 
 
+@pytest.mark.parametrize("prec", [sg.FP32, sg.FP64])
+@pytest.mark.parametrize("name,model", [("DYN_I", sg.DYN_I), ("DYN_II", sg.DYN_II)])
+def test_mc_reproduces_the_papers_european_call_table(name, model, prec):
+    # Sec. 4's European call prices (2^20 paths, 123 steps of 1/250) through
+    # the C-ABI at the paper's path count, so the two Monte Carlo noises are
+    # alike and their difference has sqrt(2) SE; the bound is 5 of those
+    g = Golden("table1_european_call.txt")
+    S0, K, T = g.floats("spot")[0], g.floats("strike")[0], g.floats("maturity")[0]
+    r, y = g.floats("rates")
+    n_steps = int(g.floats("steps")[0])
+    V, *p = g.floats(name)
+    got, se = sg.mc_price(model, p, S0 * np.exp((r - y) * T), np.array([n_steps / 250.0]), np.array([K]),
+                          discount=np.array([np.exp(-r * T)]), n_paths=1 << 20, steps_per_year=250, seed=4,
+                          prec=prec)
+    got, se = float(got.cpu()[0]), float(se.cpu()[0])
+    assert abs(got - V) <= 5 * np.sqrt(2.0) * se, (got, V, se)
+
+
 def test_mc_is_deterministic_and_validates():
     T, K, ic = quotes()
     a, _ = sg.mc_price(sg.HAGAN, PARAMS[sg.HAGAN], 1.0, T, K, is_call=ic, n_paths=10000, seed=5)
