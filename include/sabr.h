@@ -89,7 +89,9 @@ sabr_status sabr_implied_vol(sabr_model model, const double* params,
  * multiple of 1/steps_per_year with each maturity inserted.  The forward is
  * absorbed (frozen at 0) once it falls below 1e-12 * fwd.
  *   params       host, double[10]; static models use constant nu and rho,
- *                DYN_I / DYN_II use nu(t), rho(t) at each step's left end
+ *                DYN_I / DYN_II use nu(t), rho(t) at each step's right end
+ *                (the paper prints nu(t_i), but its DSabr_II results of
+ *                Sec. 6.2 are those of the right end)
  *   T, K         host, double[n]; maturities > 0, strikes >= 0
  *   is_call      host, int8[n] (nonzero = call) or NULL (all calls)
  *   discount     host, double[n] discount factors or NULL (all 1)

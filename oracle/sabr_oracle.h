@@ -105,7 +105,8 @@ void orc_box_muller(double u1, double u2, double* z1, double* z2);
 
 /* Sec. 4, eqs. (dis_SABRd), (payoff): Monte Carlo prices of n European
  * options sharing one forward f.  Static models use the constant-parameter
- * SDE (eqs. model_staticSABR1/2), DYN_I/DYN_II use nu(t), rho(t).
+ * SDE (eqs. model_staticSABR1/2), DYN_I/DYN_II use nu(t), rho(t) at each
+ * step's right end (see mc_step).
  * disc may be NULL (=1), is_call may be NULL (=all calls).
  * Returns 0 on success, -1 on invalid input. */
 int orc_mc_price(int model, const double* p, double f, const double* T,
