@@ -739,7 +739,9 @@ def run_ours(args):
             "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD,
-                       "l2": "flushed (256 MB write) between timed steps", "precision": "FP32 bulk, FP64 sums"},
+                       "l2": "flushed (256 MB write) between timed steps",
+                       "precision": ("FP32 quote arithmetic, chain state and best point; misfit summed across "
+                                     "lanes in double-float (FP32 pairs); FP64 re-score of the returned point")},
             "clocks": clocks, "gpu_launches": int(n_launch * args.steps),
             "e2e": {"value": agg["e2e"], "unit": "cost-evals/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": res_bytes},

@@ -116,17 +116,19 @@ sabr_status sabr_mc_price(sabr_model model, const double* params, double fwd,
 
 /* ------------------------------------------------------------------------
  * sabr_mc_price_noalloc -- the same prices as sabr_mc_price, for callers
- * that cannot allocate memory while they run: code recording a CUDA graph
- * around its own launches, processes whose device memory belongs to a
- * custom or fixed-size allocator, latency-critical paths that must not hit
- * the implicit synchronisation of cudaMalloc.  The paper has no counterpart;
- * this is a deployment variant of the Sec. 4 pricer.
+ * that cannot let a library allocate device memory: processes whose device
+ * memory is handed out entirely by their own fixed-size pool (a cudaMalloc
+ * from the library would fail, or take memory the pool counts on), and
+ * applications whose rules forbid libraries to allocate.  The paper has no
+ * counterpart.
  * Same arguments, layout and semantics as sabr_mc_price, with these
  * differences:
  *  - No cudaMalloc / cudaFree / cudaMallocHost / stream-ordered allocation
  *    is made.  Scratch is one fixed 8 MiB device array in the library image
  *    (every GPU that loads the library holds it until exit); host staging is
- *    static storage.  Host arrays are copied with ordinary pageable copies.
+ *    static storage.  The option and step tables are copied from that static
+ *    storage with an ordinary pageable cudaMemcpyAsync, which the runtime
+ *    may perform only after the stream's earlier work.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
  *    before any stream capture on the device.

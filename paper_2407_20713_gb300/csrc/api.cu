@@ -1,4 +1,5 @@
 // api.cu -- error reporting and argument checks shared by the entry points.
+#include <atomic>
 #include <cmath>
 
 #include "common.h"
@@ -15,6 +16,22 @@ void set_error(const char* fmt, ...) {
 }
 
 void clear_error() { g_error[0] = '\0'; }
+
+// SM count of the current device, queried once per device ordinal and
+// cached (the grid sizes of the kernels are multiples of it).
+int device_sms() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+  if (dev < 64) {
+    const int c = cache[dev].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+  }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return 1;
+  if (dev < 64) cache[dev].store(sms, std::memory_order_relaxed);
+  return sms;
+}
 
 sabr_status check_params(int model, const double* p) {
   if (n_params(model) < 0) return fail(SABR_EINVAL, "unknown model");

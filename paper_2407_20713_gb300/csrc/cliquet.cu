@@ -161,7 +161,7 @@ extern "C" sabr_status sabr_mc_cliquet(sabr_model model, const double* params, d
   }
   per_sm = std::min(std::max(per_sm, 1), 8);
   const int64_t per_block = (int64_t)kClqBlock * kMcPathsPerThread;
-  const int blocks = (int)std::min<int64_t>(152 * (int64_t)per_sm, (n_paths + per_block - 1) / per_block);
+  const int blocks = (int)std::min<int64_t>(device_sms() * (int64_t)per_sm, (n_paths + per_block - 1) / per_block);
   const size_t img = mc_image_bytes(h);
   const size_t params_off = (img + 255) & ~(size_t)255;
   const size_t part_off = params_off + 256;

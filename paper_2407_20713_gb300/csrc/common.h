@@ -47,6 +47,9 @@ inline int n_params(int model) {
   }
 }
 
+// Streaming multiprocessors of the current device (cached per device).
+int device_sms();
+
 // Range checks of a parameter vector common to every entry point.
 sabr_status check_params(int model, const double* p);
 

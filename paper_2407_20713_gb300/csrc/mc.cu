@@ -268,7 +268,7 @@ int mc_blocks_per_set(const McHost& h, int n_sets) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mc_paths_kernel<float>, kMcBlock, h.smem);
   }
   per_sm = std::min(std::max(per_sm, 1), 8);
-  const int64_t resident = 152 * (int64_t)per_sm;
+  const int64_t resident = device_sms() * (int64_t)per_sm;
   const int64_t sets = std::max(1, n_sets);
   const int64_t per_block = (int64_t)kMcBlock * kMcPathsPerThread;
   const int64_t by_paths = (h.n_paths + per_block - 1) / per_block;

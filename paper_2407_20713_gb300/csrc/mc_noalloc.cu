@@ -1,11 +1,11 @@
 // mc_noalloc.cu -- sabr_mc_price_noalloc: Monte Carlo prices without any
 // memory allocation by the library.
 //
-// Who needs it: callers that must not allocate device memory while they run
-// -- code recording a CUDA graph around its own launches, processes whose
-// device memory is owned by a custom or fixed-size allocator, and real-time
-// paths where a cudaMalloc (an implicit device synchronisation) is not
-// acceptable.  sabr_mc_price keeps a growable per-device workspace
+// Who needs it: callers that cannot let a library allocate device memory --
+// processes whose device memory is handed out entirely by their own
+// fixed-size pool (a cudaMalloc from the library would fail, or take memory
+// the pool counts on), and applications whose rules forbid libraries to
+// allocate.  sabr_mc_price keeps a growable per-device workspace
 // (cudaMalloc / cudaMallocHost on first use and when it grows); this variant
 // instead uses one fixed scratch array that is part of the library image.
 //
@@ -94,6 +94,7 @@ extern "C" sabr_status sabr_mc_price_noalloc(sabr_model model, const double* par
   std::memcpy(g_noalloc_host + params_off, p10, sizeof(p10));
   cudaStream_t s = (cudaStream_t)stream;
   // pageable source: the copy has consumed g_noalloc_host when this returns
+  // (the runtime may first wait for the stream's earlier work)
   SABR_CUDA(cudaMemcpyAsync(base, g_noalloc_host, part_off, cudaMemcpyHostToDevice, s));
   return mc_launch(h, d, (const double*)(base + params_off), nullptr, 1, bps, (double*)(base + part_off), q_value,
                    q_out, disc, price_out, stderr_out, (int)n, s);

@@ -489,7 +489,7 @@ static int next_pow2(int v) {
 }
 
 // About 24 quotes per lane (a lane runs its quote loop three quotes at a
-// time), widened while the batch has fewer than 152 x 256 threads and quotes
+// time), widened while the batch has fewer than (SMs x 256) threads and quotes
 // remain to split; the dynamic models take one lane per two maturities and
 // per ~48 quotes.
 int choose_lanes(int n_quotes, int n_mats, int model, long long batch_chains) {
@@ -509,7 +509,8 @@ int choose_lanes(int n_quotes, int n_mats, int model, long long batch_chains) {
     G = std::max(std::max(1, next_pow2(n_mats) / 2), next_pow2((n_quotes + 47) / 48));
   G = std::min(G, 32);
   const int cap = std::min(32, next_pow2(n_quotes));
-  while (G < cap && batch_chains * G < 152 * 256) G <<= 1;
+  const long long fill = (long long)device_sms() * 256;
+  while (G < cap && batch_chains * G < fill) G <<= 1;
   return G;
 }
 

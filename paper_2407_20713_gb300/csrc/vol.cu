@@ -42,7 +42,8 @@ template <class R>
 static void launch_vol(int model, const VolArgs& a, const double* T, const double* K, int64_t n,
                        double* out, cudaStream_t s) {
   int64_t blocks = (n + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  const int64_t cap = (int64_t)device_sms() * 16;
+  if (blocks > cap) blocks = cap;
   switch (model) {
     case SABR_HAGAN: implied_vol_kernel<R, SABR_HAGAN><<<blocks, 256, 0, s>>>(a, T, K, n, out); break;
     case SABR_OBLOJ: implied_vol_kernel<R, SABR_OBLOJ><<<blocks, 256, 0, s>>>(a, T, K, n, out); break;

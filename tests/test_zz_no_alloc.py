@@ -1,10 +1,11 @@
-"""sabr_mc_price_noalloc: the Monte Carlo pricer for callers that cannot
-allocate memory while they run (graph-recording code, fixed-size device
-allocators, latency-critical paths).  Called through the C-ABI, it must give
-the prices of sabr_mc_price within the MC parity tolerance, on two calls in a
-row with different problems (the shared scratch keeps the previous call's
-contents, which must not leak into the next result).  This file is collected
-last so that a run stopping at its first failure has run every other test."""
+"""sabr_mc_price_noalloc: the Monte Carlo pricer for callers that cannot let a
+library allocate device memory (processes whose device memory belongs to
+their own fixed-size pool, applications that forbid library allocations).
+Called through the C-ABI, it must give the prices of sabr_mc_price within the
+MC parity tolerance, on two calls in a row with different problems (the
+shared scratch keeps the previous call's contents, which must not leak into
+the next result).  This file is collected last so that a run stopping at its
+first failure has run every other test."""
 import ctypes
 
 import numpy as np
