@@ -47,6 +47,7 @@ SMS = 152
 
 
 LEVEL_KERNEL_SOURCES = ["sa.cu", "engine.cuh", "sabr_math.cuh"]
+LEVEL_PROFILE = "sa_queue_kernel_hagan_static_surface.md"
 
 
 def _current_profile(profile, sources):
@@ -69,26 +70,37 @@ def _current_profile(profile, sources):
     return text if d.hexdigest() == h.group(1) else None
 
 
-def profiled_traffic(profile, sources):
-    """DRAM bytes (read + write) per launch from a committed ncu summary, or
-    None when the kernel has changed since the capture."""
+def _scale(text, units):
+    """Factor from a capture's launch to a launch of `units` units: a summary
+    that records `units_per_launch` (a capture of a shorter run of the same
+    kernel) scales by units / units_per_launch, otherwise 1."""
+    import re
+    u = re.search(r"^units_per_launch: ([0-9.e+]+)", text, re.M)
+    return units / float(u.group(1)) if (u and units) else 1.0
+
+
+def profiled_traffic(profile, sources, units=None):
+    """DRAM bytes (read + write) per launch from a committed ncu summary
+    (scaled to a launch of `units` units when the capture records its own),
+    or None when the kernel has changed since the capture."""
     import re
     text = _current_profile(profile, sources)
     t = re.search(r"^traffic_bytes_per_launch: (\d+)", text, re.M) if text else None
-    return int(t.group(1)) if t else None
+    return int(int(t.group(1)) * _scale(text, units)) if t else None
 
 
-def profiled_thread_instructions(profile, sources):
+def profiled_thread_instructions(profile, sources, units=None):
     """Thread instructions per launch (warp instructions x active lanes per
-    warp instruction) from a committed ncu summary, or None when the kernel
-    has changed since the capture."""
+    warp instruction) from a committed ncu summary (scaled like
+    profiled_traffic), or None when the kernel has changed since the
+    capture."""
     import re
     text = _current_profile(profile, sources)
     if not text:
         return None
     w = re.search(r"`smsp__inst_executed\.sum`\) \| ([0-9.]+)", text)
     lanes = re.search(r"`smsp__thread_inst_executed_per_inst_executed\.ratio`\) \| ([0-9.]+)", text)
-    return float(w.group(1)) * float(lanes.group(1)) if w and lanes else None
+    return float(w.group(1)) * float(lanes.group(1)) * _scale(text, units) if w and lanes else None
 
 
 def issue_bound(thread_instr_per_unit, sm_mhz):
@@ -117,6 +129,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 form")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extra", action="store_true", help="skip the MC, dynamic and serving measurements")
+    ap.add_argument("--levels", type=int, default=None,
+                    help="temperature levels of the headline surface (default 200; fewer for a short ncu capture)")
     ap.add_argument("--case", choices=["full", "small", "mc", "cliquet", "dynamic1", "dynamic2"], default="full",
                     help="small: 2 smiles x 10 levels, main measurement only; mc: one 2^20-path MC pricing "
                          "of the MC surface; cliquet: one 2^20-path cliquet; dynamic1 / dynamic2: two runs of "
@@ -643,10 +657,12 @@ def run_ours(args):
     from paper_2407_20713_gb300 import workloads
 
     smiles = workloads.static_surface(seed=20240721 + 1000 * rank, n_chains=N_CHAINS)
+    global N_LEVELS
     if args.case == "small":
-        global N_LEVELS
         smiles = smiles[:2]
         N_LEVELS = 10
+    if args.levels:
+        N_LEVELS = args.levels
     # market vols from the true parameters (library, FP64) plus seeded noise
     market = [sg.implied_vol(sg.HAGAN, sm.truth, 1.0, sm.T, sm.K, prec=sg.FP64).cpu().numpy() + sm.noise
               for sm in smiles]
@@ -707,10 +723,14 @@ def run_ours(args):
     agg = aggregate(t_local, float(np.sum(evals)), e2e_ev / e2e_t, dist)
     t_max, value = agg["time_s"], agg["value"]
 
-    # roofline of the dominant kernel: the SA level kernel (FP32 Hagan)
+    # roofline of the dominant kernel: the persistent SA launch that runs
+    # every level of the surface from its ready queue (FP32 Hagan); its time
+    # is read from the plan's events around that launch (and the queue
+    # reset before it) on the bench's stream
     lvl_ms = float(np.mean(level_ms))
-    quote_evals_per_launch = (float(np.mean(evals)) / N_LEVELS) * 21
-    achieved = quote_evals_per_launch / (lvl_ms / 1e3) / 1e9
+    launch_ms = lvl_ms * N_LEVELS
+    quote_evals_per_launch = float(np.mean(evals)) * 21
+    achieved = quote_evals_per_launch / (launch_ms / 1e3) / 1e9
     sm_mhz = clocks.get("sm_mhz") or 1920.0
     if rates:
         peak_units, pipe, _ = pipe_bound(HAGAN_QUOTE_OPS, rates, sm_mhz)
@@ -720,12 +740,12 @@ def run_ours(args):
     else:
         peak = SMS * sm_mhz * 1e6 / (1 / 32 + 4 / 16) / 1e9
         peak_note = "nominal SFU rates (ex2 32, others 16 per SM clock) x 152 SMs x median SM clock"
-    roofline = {"bound": "alu", "kernel": "sa_level_kernel<float,HAGAN>", "achieved": achieved, "peak": peak,
+    roofline = {"bound": "alu", "kernel": "sa_queue_kernel<float,HAGAN>", "achieved": achieved, "peak": peak,
                 "unit": "Gquote-eval/s", "frac": achieved / peak,
-                "traffic": profiled_traffic("sa_level_kernel_hagan_static_surface.md", LEVEL_KERNEL_SOURCES),
-                "launch_ms": lvl_ms, "quote_evals_per_launch": quote_evals_per_launch, "peak_from": peak_note,
-                "pipe_rates_per_sm_clk": rates}
-    ti = profiled_thread_instructions("sa_level_kernel_hagan_static_surface.md", LEVEL_KERNEL_SOURCES)
+                "traffic": profiled_traffic(LEVEL_PROFILE, LEVEL_KERNEL_SOURCES, quote_evals_per_launch),
+                "launch_ms": launch_ms, "level_ms": lvl_ms, "quote_evals_per_launch": quote_evals_per_launch,
+                "peak_from": peak_note, "pipe_rates_per_sm_clk": rates}
+    ti = profiled_thread_instructions(LEVEL_PROFILE, LEVEL_KERNEL_SOURCES, quote_evals_per_launch)
     if ti:
         # the ceiling the kernel actually meets: issue slots, at the
         # instructions per quote evaluation of the committed capture

@@ -278,8 +278,13 @@ sabr_status sabr_plan_create(int32_t n, const sabr_problem* problems,
                              void* cuda_stream, sabr_plan** out);
 sabr_status sabr_plan_run(sabr_plan* plan, void* cuda_stream);
 sabr_status sabr_plan_results(sabr_plan* plan, sabr_result* out);
-/* Kernel launches one run of the plan enqueues, and the average duration
- * of its SA level kernels over the last run (ms; 0 if not timed). */
+/* Kernel launches one run of the plan enqueues, and the average time of one
+ * temperature level (all problems of the plan) over the last run, from
+ * events around the level work (ms; 0 if not timed).  The levels of a
+ * launch group run in one persistent launch that takes (problem, level,
+ * block of chains) units from a device-resident ready queue, so problems
+ * move from level to level independently; SABR_ETIMEOUT in a result means a
+ * wait of that launch gave up and its levels did not all run. */
 sabr_status sabr_plan_stats(sabr_plan* plan, int64_t* launches_per_run,
                             double* level_kernel_ms);
 void sabr_plan_destroy(sabr_plan* plan);

@@ -45,7 +45,8 @@ void launch_level(int prec, int model, const ProblemDev* probs, const int4* bmap
                   cudaStream_t s);
 void launch_persistent(int prec, int model, const ProblemDev* probs, const int4* work, const int* n_work, int grid,
                        size_t smem, cudaStream_t s);
-void launch_finalize(int prec, int model, const ProblemDev* probs, const int* plist, int n, cudaStream_t s);
+void launch_finalize(int prec, int model, const ProblemDev* probs, const int* plist, int n, cudaStream_t s,
+                     const unsigned int* queue_err = nullptr);
 // Resident 256-thread blocks per SM of the level kernel at `smem` (the
 // server's grid-stride launches).
 int persistent_blocks_per_sm(int prec, int model, size_t smem);

@@ -3,13 +3,22 @@
 // Work decomposition: a chain is a group of G lanes (G = 1..32, a power of
 // two); lanes split the quotes of the cost function.  A block holds
 // blockDim/G chains of one problem (64-thread blocks in plans, 256 in the
-// server).  One launch of sa_level_kernel runs one temperature level
-// (chain_len Metropolis steps per chain) for every chain of every problem of
-// a launch group; the chains' states live in registers for the whole level.
-// At the end of the level each block writes the argmin of its chains' final
-// states, and the last block of a problem to finish (an atomic ticket) takes
-// the argmin over the block minima (lowest block on a tie) and writes the
-// restart point of the next level.  No block ever waits for another.
+// server).  A unit of work is one temperature level (chain_len Metropolis
+// steps per chain) of one block of chains; the chains' states live in
+// registers for the whole unit.  At the end of the unit each block writes
+// the argmin of its chains' final states, and the last block of a problem's
+// level to finish (an atomic ticket) takes the argmin over the block minima
+// (lowest block on a tie) and writes the restart point of the next level.
+//
+// Plans run every level of a launch group in one persistent launch: a grid
+// of a few 64-thread blocks per SM takes units from a device-resident ready
+// queue, and the block that closes a problem's level appends the units of
+// that problem's next level.  Problems therefore move from level to level
+// independently -- an SM that finishes early takes the next ready unit of
+// any problem instead of waiting at a grid-wide barrier -- and the result
+// of every unit depends only on its problem, level and block, never on which
+// block of the grid ran it.  The server launches the same per-unit code over
+// a work list, one level per step.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -103,6 +112,52 @@ __device__ __forceinline__ bool metropolis(double u, double delta, float, double
   return u < exp(-delta / Tk);
 }
 
+// Ready queue of a plan's launch group.  entry[u] names unit u as
+// (problem, level, block) with the top bit set, or is 0 until the unit is
+// appended; units are claimed in order by an atomic head and appended by an
+// atomic tail.  The units of level 0 are placed before the launch; the block
+// that closes level k of a problem appends that problem's level k + 1.
+struct LevelQueue {
+  unsigned long long* entry;  // [total]
+  unsigned long long* head;
+  unsigned long long* tail;
+  unsigned int* err;          // nonzero once a wait has given up
+  unsigned long long total;   // units of the whole run
+  unsigned long long wait_ns; // longest wait for an entry before giving up
+};
+__host__ __device__ constexpr unsigned long long queue_entry(int p, int lv, int blk) {
+  return (1ull << 63) | ((unsigned long long)p << 43) | ((unsigned long long)lv << 23) | (unsigned long long)blk;
+}
+constexpr int kQueueMaxProblems = 1 << 20, kQueueMaxLevels = 1 << 20, kQueueMaxBlocks = 1 << 23;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Waits (one thread) until entry u has been appended; 0 when the queue's
+// error flag is set or the wait runs past q.wait_ns (which then sets it).
+__device__ unsigned long long queue_wait(const LevelQueue& q, unsigned long long u) {
+  volatile unsigned long long* slot = q.entry + u;
+  volatile unsigned int* err = q.err;
+  unsigned long long e = *slot;
+  if (e == 0) {
+    const unsigned long long t0 = global_ns();
+    while (e == 0) {
+      if (*err) return 0;
+      if (global_ns() - t0 > q.wait_ns) {
+        atomicExch(q.err, 1u);
+        return 0;
+      }
+      __nanosleep(200);
+      e = *slot;
+    }
+  }
+  __threadfence();
+  return e;
+}
+
 // ---------------------------------------------------------------------------
 // f(x0) and the restart state of level 0.  One block of G threads per problem.
 // ---------------------------------------------------------------------------
@@ -136,8 +191,14 @@ __global__ void sa_init_kernel(const ProblemDev* __restrict__ probs, const int* 
 // ---------------------------------------------------------------------------
 // Block `blk` of problem P (staged in shared memory) runs level `level`.
 // Every thread of the block calls this.
+// Units of one problem may run on different blocks of one persistent launch,
+// so the state another block wrote (restart point, per-chain best and
+// counters, block minima) is read from L2 (ld.global.cg), never from a
+// possibly stale L1 line.  `q` (plans only) receives the units of the next
+// level when this block closes level `level` of problem `pid`.
 template <class R, int MODEL>
-__device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int level, unsigned char* smem) {
+__device__ __forceinline__ void sa_level_block(const ProblemDev& P, int pid, int blk, int level, unsigned char* smem,
+                                               const LevelQueue* q) {
   unsigned char* rest;
   const SmemQuotes<R> sq = stage_quotes<R>(P, smem, blockDim.x, threadIdx.x, &rest);
   constexpr int D = Dim<MODEL>::value;
@@ -156,7 +217,7 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
   const bool active = chain < P.n_chains;
   const unsigned gmask = group_mask(G);
 
-  const double T0 = P.state[kMaxD + 1];
+  const double T0 = __ldcg(&P.state[kMaxD + 1]);
   const double Tk = __dmul_rn(T0, P.ck[level]);
   double sk = __dmul_rn(P.step0, __dsqrt_rn(__ddiv_rn(Tk, T0)));
   if (sk < P.step_min) sk = P.step_min;
@@ -173,9 +234,9 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
   __syncthreads();
   R x[D];
 #pragma unroll
-  for (int i = 0; i < D; ++i) x[i] = (R)P.state[i];
+  for (int i = 0; i < D; ++i) x[i] = (R)__ldcg(&P.state[i]);
   using C = typename CostOf<R>::T;
-  C fcur = cost_from(P.state[kMaxD], C{});
+  C fcur = cost_from(__ldcg(&P.state[kMaxD]), C{});
   C bf = fcur;
   const float inv_Tk = (float)(1.4426950408889634 / Tk);  // log2(e) / T_k: FP32 Metropolis in base 2
   // the chain's best point lives in its chain_bx row (written by lane 0 on
@@ -188,7 +249,7 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
         for (int i = 0; i < kMaxD; ++i) cbx[i] = i < D ? x[i] : (R)0;
       }
     } else {
-      bf = cost_from(P.chain_bf[chain], C{});
+      bf = cost_from(__ldcg(&P.chain_bf[chain]), C{});
     }
   }
   unsigned ev = 0, ac = 0;  // per level: at most chain_len each
@@ -288,8 +349,8 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
         P.chain_ev[chain] = ev;
         P.chain_ac[chain] = ac;
       } else {
-        P.chain_ev[chain] += ev;
-        P.chain_ac[chain] += ac;
+        P.chain_ev[chain] = __ldcg(&P.chain_ev[chain]) + ev;
+        P.chain_ac[chain] = __ldcg(&P.chain_ac[chain]) + ac;
       }
       red_f[g] = cost_to_double(fcur);
 #pragma unroll
@@ -338,6 +399,19 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int blk, int
       P.state[kMaxD] = f;
       *P.arrive = 0u;
     }
+    if (q != nullptr && level + 1 < P.n_levels) {
+      // append the next level's units of this problem, after the restart
+      // point is visible device-wide
+      __shared__ unsigned long long s_base;
+      if (threadIdx.x == 0) {
+        __threadfence();
+        s_base = atomicAdd(q->tail, (unsigned long long)P.n_blocks);
+      }
+      __syncthreads();
+      __threadfence();
+      volatile unsigned long long* ent = q->entry;
+      for (int b = threadIdx.x; b < P.n_blocks; b += blockDim.x) ent[s_base + b] = queue_entry(pid, level + 1, b);
+    }
   }
 }
 
@@ -365,8 +439,50 @@ __global__ void __launch_bounds__(kSaBlock, (LevelMinBlocks<R, MODEL>::value))
     const int4 it = work[w];
     const int lv = level >= 0 ? level : it.z;
     load_problem(probs, it.x, &P);
-    if (lv < P.n_levels) sa_level_block<R, MODEL>(P, it.y, lv, smem);
+    if (lv < P.n_levels) sa_level_block<R, MODEL>(P, it.x, it.y, lv, smem, nullptr);
     __syncthreads();
+  }
+}
+
+// Every level of a plan's launch group in one launch: each block takes units
+// from the ready queue until all are claimed (or a wait gave up).
+template <class R, int MODEL>
+__global__ void __launch_bounds__(kLevelBlock, (4 * LevelMinBlocks<R, MODEL>::value))
+    sa_queue_kernel(const ProblemDev* __restrict__ probs, LevelQueue q) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ ProblemDev P;
+  __shared__ unsigned long long s_e;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      unsigned long long e = 0;
+      if (*(volatile unsigned int*)q.err == 0) {
+        const unsigned long long u = atomicAdd(q.head, 1ull);
+        if (u < q.total) e = queue_wait(q, u);
+      }
+      s_e = e;
+    }
+    __syncthreads();
+    const unsigned long long e = s_e;
+    if (e == 0) return;
+    const int pid = (int)((e >> 43) & (kQueueMaxProblems - 1));
+    const int lv = (int)((e >> 23) & (kQueueMaxLevels - 1));
+    const int blk = (int)(e & (kQueueMaxBlocks - 1));
+    load_problem(probs, pid, &P);
+    sa_level_block<R, MODEL>(P, pid, blk, lv, smem, &q);
+    __syncthreads();
+  }
+}
+
+// Before each run: head and error flag cleared, the units of level 0 (a
+// list fixed when the plan was built) in place, every later entry empty.
+__global__ void queue_reset_kernel(LevelQueue q, const unsigned long long* __restrict__ level0, unsigned long long n0) {
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < q.total; i += stride)
+    q.entry[i] = i < n0 ? level0[i] : 0ull;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *q.head = 0ull;
+    *q.tail = n0;
+    *q.err = 0u;
   }
 }
 
@@ -374,9 +490,12 @@ __global__ void __launch_bounds__(kSaBlock, (LevelMinBlocks<R, MODEL>::value))
 // Best point over all chains, FP64 re-score, counters -> result.
 // One 256-thread block per problem.
 // ---------------------------------------------------------------------------
+// `queue_err` (plans): a ready-queue wait gave up, so the levels did not all
+// run; the result then carries SABR_ETIMEOUT.
 template <class R, int MODEL>
 __global__ void __launch_bounds__(kSaBlock) sa_finalize_kernel(const ProblemDev* __restrict__ probs,
-                                                              const int* __restrict__ plist) {
+                                                              const int* __restrict__ plist,
+                                                              const unsigned int* __restrict__ queue_err) {
   __shared__ ProblemDev P;
   __shared__ double s_f[kSaBlock];
   __shared__ int s_c[kSaBlock];
@@ -431,6 +550,7 @@ __global__ void __launch_bounds__(kSaBlock) sa_finalize_kernel(const ProblemDev*
     }
     r->misfit = f;
     r->restart_misfit = P.state[kMaxD];
+    if (queue_err != nullptr && *queue_err != 0u) r->status = SABR_ETIMEOUT;
     r->n_evals = (int64_t)te;
     r->n_accepts = (int64_t)ta;
   }
@@ -753,8 +873,23 @@ void launch_persistent(int prec, int model, const ProblemDev* probs, const int4*
   SABR_DISPATCH(prec, model, (sa_level_kernel<R, M><<<grid, kSaBlock, smem, s>>>(probs, work, n_work, 0, -1)));
 }
 
-void launch_finalize(int prec, int model, const ProblemDev* probs, const int* plist, int n, cudaStream_t s) {
-  SABR_DISPATCH(prec, model, (sa_finalize_kernel<R, M><<<n, kSaBlock, 0, s>>>(probs, plist)));
+void launch_finalize(int prec, int model, const ProblemDev* probs, const int* plist, int n, cudaStream_t s,
+                     const unsigned int* queue_err) {
+  SABR_DISPATCH(prec, model, (sa_finalize_kernel<R, M><<<n, kSaBlock, 0, s>>>(probs, plist, queue_err)));
+}
+
+static void launch_queue(int prec, int model, const ProblemDev* probs, const LevelQueue& q, int grid, size_t smem,
+                         cudaStream_t s) {
+  SABR_DISPATCH(prec, model, (sa_queue_kernel<R, M><<<grid, kLevelBlock, smem, s>>>(probs, q)));
+}
+
+static int queue_blocks_per_sm(int prec, int model, size_t smem) {
+  int nb = 1;
+  SABR_DISPATCH(prec, model, (cudaFuncSetAttribute(sa_queue_kernel<R, M>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                              cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sa_queue_kernel<R, M>, kLevelBlock,
+                                                                            smem)));
+  return nb < 1 ? 1 : nb;
 }
 
 int persistent_blocks_per_sm(int prec, int model, size_t smem) {
@@ -772,7 +907,36 @@ struct LaunchGroup {
   size_t smem_level = 0, smem_init = 0;
   int4* d_bmap = nullptr;
   int* d_plist = nullptr;
+  // ready queue (all levels in one persistent launch); per-level launches
+  // when use_queue is false
+  bool use_queue = false;
+  LevelQueue q{};
+  unsigned long long* d_level0 = nullptr;
+  unsigned long long n0 = 0;
+  int queue_grid = 0;
 };
+
+// Resident 64-thread blocks per SM that a plan's persistent level launch
+// aims for: four give every SM scheduler two warps, so all schedulers carry
+// the same load (the environment variable SABR_WORKERS_PER_SM overrides it
+// for tuning).
+static int workers_per_sm() {
+  if (const char* e = std::getenv("SABR_WORKERS_PER_SM")) {
+    const int w = std::atoi(e);
+    if (w >= 1 && w <= 32) return w;
+  }
+  return 4;
+}
+// Whether plans may use the ready queue: the environment variable
+// SABR_PLAN_QUEUE=0 makes them launch their levels one by one instead (the
+// same units in a different launch shape; the results are identical).
+static bool queue_enabled() {
+  const char* e = std::getenv("SABR_PLAN_QUEUE");
+  return !(e && e[0] == '0');
+}
+// A ready queue takes 8 bytes per unit; beyond this a plan launches its
+// levels one by one instead.
+constexpr unsigned long long kMaxQueueBytes = 512ull << 20;
 
 }  // namespace sabr
 
@@ -809,9 +973,17 @@ static sabr_status enqueue_plan(sabr_plan* p, cudaStream_t s, bool capturing) {
     SABR_CUDA(cudaEventRecordWithFlags(p->ev_lv0, s, cudaEventRecordExternal));
   else
     SABR_CUDA(cudaEventRecord(p->ev_lv0, s));
+  for (auto& g : p->groups) {
+    if (!g.use_queue || g.q.total == 0) continue;
+    queue_reset_kernel<<<(int)std::min<unsigned long long>(1024, (g.q.total + 255) / 256), 256, 0, s>>>(
+        g.q, g.d_level0, g.n0);
+    launch_queue(g.prec, g.model, p->d_probs, g.q, g.queue_grid, g.smem_level, s);
+    launches += 2;
+    ++level_launches;
+  }
   for (int lv = 0; lv < p->max_levels; ++lv)
     for (auto& g : p->groups) {
-      if (lv >= g.max_levels) continue;
+      if (g.use_queue || lv >= g.max_levels) continue;
       launch_level(g.prec, g.model, p->d_probs, g.d_bmap, g.total_blocks, lv, g.smem_level, s);
       ++launches;
       ++level_launches;
@@ -821,7 +993,8 @@ static sabr_status enqueue_plan(sabr_plan* p, cudaStream_t s, bool capturing) {
   else
     SABR_CUDA(cudaEventRecord(p->ev_lv1, s));
   for (auto& g : p->groups) {
-    launch_finalize(g.prec, g.model, p->d_probs, g.d_plist, (int)g.problems.size(), s);
+    launch_finalize(g.prec, g.model, p->d_probs, g.d_plist, (int)g.problems.size(), s,
+                    g.use_queue ? g.q.err : nullptr);
     ++launches;
   }
   for (auto& m : p->mc) {
@@ -920,9 +1093,35 @@ static sabr_status build_plan(int32_t n, const sabr_problem* problems, const sab
     p->max_levels = std::max(p->max_levels, hp[i].n_levels);
   }
   std::vector<size_t> bmap_off(p->groups.size()), plist_off(p->groups.size());
+  std::vector<size_t> qent_off(p->groups.size()), qctl_off(p->groups.size()), ql0_off(p->groups.size());
+  std::vector<std::vector<unsigned long long>> level0(p->groups.size());
+  const int sms = device_sms();
   for (size_t gi = 0; gi < p->groups.size(); ++gi) {
-    bmap_off[gi] = take(sizeof(int4) * p->groups[gi].total_blocks);
-    plist_off[gi] = take(sizeof(int) * p->groups[gi].problems.size());
+    LaunchGroup& g = p->groups[gi];
+    bmap_off[gi] = take(sizeof(int4) * g.total_blocks);
+    plist_off[gi] = take(sizeof(int) * g.problems.size());
+    // ready queue: one entry per (problem, level, block) of the run
+    unsigned long long total = 0;
+    double unit_ns = 0.0;  // generous bound on the duration of one unit
+    for (int pi : g.problems) {
+      total += (unsigned long long)hp[pi].n_levels * (unsigned long long)pd[pi].n_blocks;
+      for (int b = 0; hp[pi].n_levels > 0 && b < pd[pi].n_blocks; ++b) level0[gi].push_back(queue_entry(pi, 0, b));
+      const double per_step = (double)(hp[pi].n_quotes / lanes[pi] + 1) + 64.0 * hp[pi].n_mats + 64.0;
+      unit_ns = std::max(unit_ns, 100.0 * per_step * (double)hp[pi].chain_len);
+    }
+    g.use_queue = queue_enabled() && nf <= kQueueMaxProblems && p->max_levels < kQueueMaxLevels &&
+                  total * 8 <= kMaxQueueBytes;
+    for (int pi : g.problems) g.use_queue = g.use_queue && pd[pi].n_blocks <= kQueueMaxBlocks;
+    if (g.use_queue) {
+      g.q.total = total;
+      g.q.wait_ns = (unsigned long long)std::min(6.0e11, 5.0e9 + 100.0 * unit_ns);
+      g.n0 = level0[gi].size();
+      qent_off[gi] = take(8 * std::max<unsigned long long>(total, 1));
+      qctl_off[gi] = take(32);
+      ql0_off[gi] = take(8 * std::max<size_t>(level0[gi].size(), 1));
+      const int per_sm = std::min(workers_per_sm(), queue_blocks_per_sm(g.prec, g.model, g.smem_level));
+      g.queue_grid = std::max(1, std::min(g.total_blocks, sms * per_sm));
+    }
   }
   const size_t arena_bytes = align_up(o, 256);
 
@@ -947,6 +1146,15 @@ static sabr_status build_plan(int32_t n, const sabr_problem* problems, const sab
     std::memcpy(img.data() + plist_off[gi], g.problems.data(), sizeof(int) * g.problems.size());
     g.d_bmap = (int4*)(base + bmap_off[gi]);
     g.d_plist = (int*)(base + plist_off[gi]);
+    if (g.use_queue) {
+      g.q.entry = (unsigned long long*)(base + qent_off[gi]);
+      g.q.head = (unsigned long long*)(base + qctl_off[gi]);
+      g.q.tail = g.q.head + 1;
+      g.q.err = (unsigned int*)(g.q.head + 2);
+      g.d_level0 = (unsigned long long*)(base + ql0_off[gi]);
+      if (!level0[gi].empty())
+        std::memcpy(img.data() + ql0_off[gi], level0[gi].data(), 8 * level0[gi].size());
+    }
     set_engine_smem(g.prec, g.model, std::max(g.smem_level, g.smem_init));
   }
   p->d_probs = (ProblemDev*)(base + probs_off);
@@ -1042,11 +1250,11 @@ sabr_status sabr_plan_stats(sabr_plan* plan, int64_t* launches, double* level_ms
   if (launches) *launches = plan->launches;
   if (level_ms) {
     *level_ms = 0.0;
-    if (plan->ran && plan->level_launches > 0) {
+    if (plan->ran && plan->level_launches > 0 && plan->max_levels > 0) {
       SABR_CUDA(cudaEventSynchronize(plan->ev_done));
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, plan->ev_lv0, plan->ev_lv1) == cudaSuccess)
-        *level_ms = (double)ms / (double)plan->level_launches;
+        *level_ms = (double)ms / (double)plan->max_levels;
     }
   }
   return SABR_OK;

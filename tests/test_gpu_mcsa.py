@@ -1,5 +1,7 @@
 """GPU parity of Technique II (Sec. 5.2): SA whose cost is the misfit of
 Monte Carlo prices on common random numbers, against the oracle."""
+import os
+
 import numpy as np
 import pytest
 
@@ -51,3 +53,31 @@ def test_fp32_mc_cost_stays_close_to_the_oracle():
     # part ways late, so compare outcomes: both reach the same basin.
     assert abs(g.misfit_fp64 - o["misfit"]) <= 0.5 * o["misfit"] + 1e-6
     np.testing.assert_allclose(g.params[2:], o["params"][2:], atol=0.1)
+
+
+def test_fp32_mc_surface_fixed_beta_within_one_percent_of_the_oracle():
+    # Technique II on the MC surface's shape (8 maturities x 15 calls, Sec.
+    # 5.2 with the price misfit of Sec. 3 eq. error_calibrate_relativo), beta
+    # fixed at its true value and a box of about +-50% around the truth, so
+    # that the SA reaches its minimum; common random numbers make the cost a
+    # deterministic function of the parameters.  The paths per evaluation
+    # (1024 at 50 steps a year) are fewer than the benchmark's so that the
+    # FP64 oracle runs the same schedule in seconds.  FP32 paths must end
+    # within 1% of the oracle's final misfit.
+    from paper_2407_20713_gb300 import workloads
+    w = workloads.mc_surface()
+    a, b, r, n = w.truth
+    mkt, _ = O.mc_price(O.HAGAN, w.truth, 1.0, w.T, w.K, n_paths=1 << 18, steps_per_year=50,
+                        seed=w.meta["market_seed"] & 0xFFFFFFFF)
+    lo = [0.5 * a, b, max(-0.95, r - 0.4), 0.5 * n]
+    hi = [1.5 * a, b, min(0.95, r + 0.4), 1.5 * n]
+    kw = dict(n_chains=64, n_levels=30, chain_len=10, factor=0.8)
+    for seed in (1, 2):
+        pb = sg.CalibrationProblem(model=sg.HAGAN, T=w.T, K=w.K, market=mkt, lo=lo, hi=hi, prec=sg.FP32,
+                                   cost=sg.COST_MC_PRICE, mc_paths=1024, mc_steps_per_year=50, mc_seed=5, seed=seed,
+                                   **kw)
+        g = sg.calibrate(pb)
+        o = O.sa_calibrate(O.HAGAN, 1.0, w.T, w.K, mkt, lo, hi, cost=O.COST_MC, mc_paths=1024,
+                           mc_steps_per_year=50, mc_seed=5, seed=seed, n_threads=os.cpu_count() or 8, **kw)
+        assert g.status == 0
+        assert abs(g.misfit_fp64 - o["misfit"]) <= 0.01 * o["misfit"], (seed, g.misfit_fp64, o["misfit"])

@@ -140,7 +140,37 @@ def test_graph_replay_equals_direct_launches_and_repeats():
     for x, y, z in zip(direct, r1, r2):
         assert np.array_equal(x.params, y.params) and np.array_equal(y.params, z.params)
         assert x.misfit == y.misfit == z.misfit and x.n_evals == y.n_evals == z.n_evals
-    assert n_launch == 1 + 10 + 1 and ms > 0
+    # init, queue reset, one persistent launch for all levels, finalize
+    assert n_launch == 1 + 2 + 1 and ms > 0
+
+
+def test_ready_queue_equals_level_by_level_launches(monkeypatch):
+    # the persistent ready-queue launch and one launch per level run the same
+    # units; results are bitwise identical, also for a batch whose problems
+    # have different level counts, chain counts and models
+    mkt = market()
+    T, K, mk2, lo2, hi2 = dyn_surface(O.DYN_I)
+    pbs = [sg.CalibrationProblem(model=sg.HAGAN, T=T15, K=K15, market=mkt, lo=LO4, hi=HI4, prec=sg.FP32,
+                                 n_chains=3000, n_levels=12, chain_len=20, seed=31),
+           sg.CalibrationProblem(model=sg.HAGAN, T=T15[:9], K=K15[:9], market=mkt[:9], lo=LO4, hi=HI4,
+                                 prec=sg.FP32, n_chains=700, n_levels=5, chain_len=20, seed=32),
+           sg.CalibrationProblem(model=sg.DYN_I, T=T, K=K, market=mk2, lo=lo2, hi=hi2, prec=sg.FP64,
+                                 n_chains=90, n_levels=7, chain_len=10, seed=33),
+           sg.CalibrationProblem(model=sg.HAGAN, T=T15, K=K15, market=mkt, lo=LO4, hi=HI4, prec=sg.FP32,
+                                 n_chains=64, n_levels=0, chain_len=20, seed=34)]
+    queued = sg.calibrate_batch(pbs)
+    monkeypatch.setenv("SABR_PLAN_QUEUE", "0")
+    plan = sg.Plan(pbs, use_graph=True)
+    plan.run()
+    levelwise = plan.results()
+    n_launch, _ = plan.stats()
+    plan.close()
+    assert n_launch == 2 + (12 + 7) + 2
+    for x, y in zip(queued, levelwise):
+        assert x.status == y.status == 0
+        assert np.array_equal(x.params, y.params) and np.array_equal(x.restart_params, y.restart_params)
+        assert x.misfit == y.misfit and x.misfit_fp64 == y.misfit_fp64
+        assert x.n_evals == y.n_evals and x.n_accepts == y.n_accepts
 
 
 def test_edge_cases():
