@@ -88,6 +88,12 @@ def lib():
             _D, _D, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_uint64, ctypes.c_int,
             _PD, _PD, _PD, _PD, _PI64, _PI64, _PD]
         L.orc_sa_calibrate.restype = ctypes.c_int
+        L.orc_sa_shard_level.argtypes = [
+            ctypes.c_int, ctypes.c_int, _D, _I64, _PD, _PD, _PD, _PD, _PI8,
+            _I64, _D, ctypes.c_uint64, _PD, _PD, _D, _D, ctypes.c_int, ctypes.c_int, _D, _D,
+            ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _PD, _D,
+            _PD, _PD, _PD, _PD, _PI64, _PI64]
+        L.orc_sa_shard_level.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -269,6 +275,58 @@ def sa_calibrate(model, f, T, K, mkt, lo, hi, *, cost=COST_VOL, n_chains=64,
     if trace:
         out["trace"] = tr[:n_levels].copy()
     return out
+
+
+class SaShard:
+    """The chains c0 .. c0+nc-1 of orc_sa_calibrate, one level at a time
+    (Sec. 5.1, the multi-GPU form of Technique I): level() runs a level from
+    the current restart point and returns this share's lowest final state
+    (cost, chain, x), restart() sets the next level's start, result() the
+    share's best-ever point (cost, chain, x) and counters.  Formula cost
+    (Technique I) only."""
+
+    def __init__(self, model, f, T, K, mkt, lo, hi, *, n_chains, c0, nc, T0=0.0, factor=0.95, n_levels=200,
+                 chain_len=100, step0=0.1, step_min=1e-6, seed=0, x0=None, n_threads=1):
+        self.model, self.f = model, float(f)
+        self.T = np.ascontiguousarray(T, dtype=np.float64).ravel()
+        self.K = np.ascontiguousarray(K, dtype=np.float64).ravel()
+        self.mkt = np.ascontiguousarray(mkt, dtype=np.float64).ravel()
+        self.lo, self.hi = _params(lo), _params(hi)
+        self.d = n_params(model)
+        xs = _params(x0) if x0 is not None else 0.5 * (self.lo + self.hi)
+        xs[self.d:] = 0.0
+        fs = misfit(implied_vol(model, xs, f, self.T, self.K), self.mkt)
+        self.T0 = float(T0) if T0 > 0.0 else (fs if fs > 0.0 else 1.0)
+        self.factor, self.chain_len, self.step0, self.step_min = factor, chain_len, step0, step_min
+        self.seed, self.n_threads, self.c0, self.nc = seed, n_threads, c0, nc
+        self.xs, self.fs = xs, fs
+        self.cx = np.zeros(10 * nc)
+        self.cf = np.zeros(nc)
+        self.bx = np.tile(xs, nc)
+        self.bf = np.full(nc, fs)
+        self.ev = np.zeros(nc, dtype=np.int64)
+        self.ac = np.zeros(nc, dtype=np.int64)
+
+    def level(self, lev):
+        rc = lib().orc_sa_shard_level(
+            self.model, COST_VOL, self.f, self.T.size, _dp(self.T), _dp(self.K), _dp(self.mkt), None, None,
+            0, 250.0, 0, _dp(self.lo), _dp(self.hi), self.T0, float(self.factor), int(lev), int(self.chain_len),
+            float(self.step0), float(self.step_min), int(self.seed) & 0xFFFFFFFFFFFFFFFF, int(self.n_threads),
+            int(self.c0), int(self.nc), _dp(self.xs), float(self.fs), _dp(self.cx), _dp(self.cf), _dp(self.bx),
+            _dp(self.bf), self.ev.ctypes.data_as(_PI64), self.ac.ctypes.data_as(_PI64))
+        if rc != 0:
+            raise ValueError("orc_sa_shard_level rejected its input")
+        i = int(np.argmin(self.cf))  # first of the lowest
+        return float(self.cf[i]), self.c0 + i, self.cx[10 * i:10 * i + 10].copy()
+
+    def restart(self, f, x):
+        self.xs = np.asarray(x, dtype=np.float64).copy()
+        self.fs = float(f)
+
+    def result(self):
+        i = int(np.argmin(self.bf))
+        return (float(self.bf[i]), self.c0 + i, self.bx[10 * i:10 * i + 10].copy(), int(self.ev.sum()),
+                int(self.ac.sum()))
 
 
 def mc_cliquet(model, p, f, T, n_resets, floor_l, cap_l, floor_g, cap_g, disc=1.0, n_paths=1 << 12,

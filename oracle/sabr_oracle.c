@@ -718,6 +718,57 @@ void orc_sa_uniforms(const uint32_t key[2], int chain, int level, int step,
   u[d] = ((double)bits + 0.5) * 0x1p-23;
 }
 
+/* Temperature and step scale of level lev: geometric cooling
+ * T_k = T0 c^k and s_k = max(s_min, s0 sqrt(T_k / T0)). */
+static void sa_level_schedule(double T0, double factor, int lev, double step0,
+                              double step_min, double* Tk, double* sk) {
+  *Tk = T0 * pow(factor, (double)lev);
+  *sk = step0 * sqrt(*Tk / T0);
+  if (*sk < step_min) *sk = step_min;
+}
+
+/* chain_len Metropolis steps of level lev for the nc chains c0 .. c0+nc-1:
+ * state i (chain c0 + i) is x = cx + 10 i with cost cf[i], its best-ever
+ * point bx + 10 i, bf[i], and its counters ev[i], ac[i]. */
+static void sa_level_chains(const sa_ctx* c, int d, const double* lo,
+                            const double* hi, const uint32_t key[2], double Tk,
+                            double sk, int lev, int chain_len, int c0, int nc,
+                            double* cx, double* cf, double* bx, double* bf,
+                            int64_t* ev, int64_t* ac, double* scratch,
+                            int n_threads) {
+#pragma omp parallel for schedule(static) num_threads(n_threads)
+  for (int i = 0; i < nc; ++i) {
+    const int ch = c0 + i;
+    double* x = cx + 10 * i;
+    double* scr = scratch + c->n * i;
+    double u[11], xp[10];
+    for (int st = 0; st < chain_len; ++st) {
+      orc_sa_uniforms(key, ch, lev, st, d, u);
+      int inside = 1;
+      for (int j = 0; j < 10; ++j) xp[j] = 0.0;
+      for (int j = 0; j < d; ++j) {
+        double step = sk * (hi[j] - lo[j]);
+        xp[j] = x[j] + step * (2.0 * u[j] - 1.0);
+        if (xp[j] < lo[j] || xp[j] > hi[j]) inside = 0;
+      }
+      if (!inside || !orc_feasible(c->model, xp, c->Tmax)) continue;
+      double fp = sa_cost(c, xp, scr);
+      ev[i]++;
+      if (!(fp == fp)) continue;
+      if (fp < bf[i]) { /* best-ever over every evaluated point */
+        bf[i] = fp;
+        memcpy(bx + 10 * i, xp, sizeof(xp));
+      }
+      double delta = fp - cf[i];
+      if (delta <= 0.0 || u[d] < exp(-delta / Tk)) { /* Metropolis */
+        memcpy(x, xp, sizeof(xp));
+        cf[i] = fp;
+        ac[i]++;
+      }
+    }
+  }
+}
+
 int orc_sa_calibrate(int model, int cost, double f, int64_t n,
                      const double* T, const double* K, const double* mkt,
                      const double* disc, const int8_t* is_call, int n_chains,
@@ -769,39 +820,10 @@ int orc_sa_calibrate(int model, int cost, double f, int64_t n,
   const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
 
   for (int lev = 0; lev < n_levels; ++lev) {
-    double Tk = T0 * pow(factor, (double)lev);       /* geometric cooling */
-    double sk = step0 * sqrt(Tk / T0);               /* step scale */
-    if (sk < step_min) sk = step_min;
-#pragma omp parallel for schedule(static) num_threads(n_threads)
-    for (int ch = 0; ch < n_chains; ++ch) {
-      double* x = cx + 10 * ch;
-      double* scr = scratch + n * ch;
-      double u[11], xp[10];
-      for (int st = 0; st < chain_len; ++st) {
-        orc_sa_uniforms(key, ch, lev, st, d, u);
-        int inside = 1;
-        for (int i = 0; i < 10; ++i) xp[i] = 0.0;
-        for (int i = 0; i < d; ++i) {
-          double step = sk * (hi[i] - lo[i]);
-          xp[i] = x[i] + step * (2.0 * u[i] - 1.0);
-          if (xp[i] < lo[i] || xp[i] > hi[i]) inside = 0;
-        }
-        if (!inside || !orc_feasible(model, xp, c.Tmax)) continue;
-        double fp = sa_cost(&c, xp, scr);
-        ev[ch]++;
-        if (!(fp == fp)) continue;
-        if (fp < bf[ch]) { /* best-ever over every evaluated point */
-          bf[ch] = fp;
-          memcpy(bx + 10 * ch, xp, sizeof(xp));
-        }
-        double delta = fp - cf[ch];
-        if (delta <= 0.0 || u[d] < exp(-delta / Tk)) { /* Metropolis */
-          memcpy(x, xp, sizeof(xp));
-          cf[ch] = fp;
-          ac[ch]++;
-        }
-      }
-    }
+    double Tk, sk;
+    sa_level_schedule(T0, factor, lev, step0, step_min, &Tk, &sk);
+    sa_level_chains(&c, d, lo, hi, key, Tk, sk, lev, chain_len, 0, n_chains,
+                    cx, cf, bx, bf, ev, ac, scratch, n_threads);
     /* Level end: the chain with the lowest final cost (lowest index on a
      * tie) gives the common start of the next level. */
     int arg = 0;
@@ -836,6 +858,46 @@ int orc_sa_calibrate(int model, int cost, double f, int64_t n,
   free(bf);
   free(ev);
   free(ac);
+  free(scratch);
+  return 0;
+}
+
+/* One level of orc_sa_calibrate for the chains c0 .. c0+nc-1 only (the
+ * multi-GPU form of Sec. 5.1: each device runs a share of the chains and the
+ * host takes the minimum of the shares' minima at every level).  Every
+ * chain starts from the restart point (xs, fs); on return cx/cf hold the
+ * chains' final states (the caller takes the argmin over all shares, lowest
+ * chain on a tie) and bx/bf/ev/ac (indexed by chain - c0) are updated.
+ * T0 is the first level's temperature (f(x0) when the caller's schedule
+ * says so). */
+int orc_sa_shard_level(int model, int cost, double f, int64_t n,
+                       const double* T, const double* K, const double* mkt,
+                       const double* disc, const int8_t* is_call,
+                       int64_t mc_paths, double mc_spy, uint64_t mc_seed,
+                       const double* lo, const double* hi, double T0,
+                       double factor, int lev, int chain_len, double step0,
+                       double step_min, uint64_t seed, int n_threads, int c0,
+                       int nc, const double* xs, double fs, double* cx,
+                       double* cf, double* bx, double* bf, int64_t* ev,
+                       int64_t* ac) {
+  int d = orc_n_params(model);
+  if (d < 0 || n <= 0 || nc <= 0 || c0 < 0 || lev < 0 || chain_len < 0 ||
+      !(T0 > 0.0))
+    return -1;
+  sa_ctx c = {model, cost, f, n, T, K, mkt, disc, is_call, mc_paths, mc_spy,
+              mc_seed, 0.0, NULL};
+  for (int64_t q = 0; q < n; ++q) c.Tmax = T[q] > c.Tmax ? T[q] : c.Tmax;
+  if (n_threads < 1) n_threads = 1;
+  for (int i = 0; i < nc; ++i) {
+    memcpy(cx + 10 * i, xs, sizeof(double) * 10);
+    cf[i] = fs;
+  }
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  double Tk, sk;
+  sa_level_schedule(T0, factor, lev, step0, step_min, &Tk, &sk);
+  double* scratch = (double*)malloc(sizeof(double) * n * nc);
+  sa_level_chains(&c, d, lo, hi, key, Tk, sk, lev, chain_len, c0, nc, cx, cf,
+                  bx, bf, ev, ac, scratch, n_threads);
   free(scratch);
   return 0;
 }

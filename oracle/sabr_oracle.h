@@ -146,6 +146,21 @@ int orc_sa_calibrate(int model, int cost, double f, int64_t n,
                      double* restart_x, double* restart_f,
                      int64_t* n_evals, int64_t* n_accepts, double* trace);
 
+/* One level of orc_sa_calibrate for chains c0 .. c0+nc-1 from the restart
+ * point (xs, fs): the share of one device in the multi-GPU form of Sec. 5.1.
+ * cx[10 nc], cf[nc] receive the final states; bx, bf, ev, ac (indexed by
+ * chain - c0) carry the best-ever points and counters across levels. */
+int orc_sa_shard_level(int model, int cost, double f, int64_t n,
+                       const double* T, const double* K, const double* mkt,
+                       const double* disc, const int8_t* is_call,
+                       int64_t mc_paths, double mc_spy, uint64_t mc_seed,
+                       const double* lo, const double* hi, double T0,
+                       double factor, int lev, int chain_len, double step0,
+                       double step_min, uint64_t seed, int n_threads, int c0,
+                       int nc, const double* xs, double fs, double* cx,
+                       double* cf, double* bx, double* bf, int64_t* ev,
+                       int64_t* ac);
+
 #ifdef __cplusplus
 }
 #endif
