@@ -136,6 +136,10 @@ def parse():
                          "of the MC surface; cliquet: one 2^20-path cliquet; dynamic1 / dynamic2: two runs of "
                          "three levels of the joint Case I / Case II fit (the last five for profiler captures)")
     ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-loads", type=float, nargs="*", default=[0.5, 0.8, 0.95],
+                    help="fractions of capacity for --serve-only (each with --serve-requests requests)")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="only the serving measurement (capacity and loads) at --serve-requests requests")
     return ap.parse_args()
 
 
@@ -452,7 +456,7 @@ def measure_mc_calibration(sg, torch, stream, rates, sm_mhz):
     return res
 
 
-def measure_dynamic(sg, torch, stream, levels=10):
+def measure_dynamic(sg, torch, stream, levels=N_LEVELS):
     """Joint dynamic fits on 12 maturities x 21 strikes, 8192 chains each, one
     Case I and one Case II surface, FP32; `levels` of the 200 levels."""
     from paper_2407_20713_gb300 import workloads
@@ -525,7 +529,7 @@ def measure_serving(sg, n_requests, rate_hz, formula_only=False):
 
     th = threading.Thread(target=submitter)
     th.start()
-    deadline = time.perf_counter() + 600.0
+    deadline = time.perf_counter() + 600.0 + 0.5 * len(reqs)
     while len(done) < len(reqs) and time.perf_counter() < deadline and not errors:
         with lock:
             outstanding = [(i, t) for i, t in tickets.items() if i not in done]
@@ -541,39 +545,82 @@ def measure_serving(sg, n_requests, rate_hz, formula_only=False):
     wall = max(done.values()) - t0
     st = srv.stats()
     srv.close()
-    return {"requests": len(reqs), "completed": len(done), "offered_rate_hz": rate_hz,
-            "calibrations_per_s": len(done) / wall,
-            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-            "steps": st["steps"], "kernel_launches": st["kernel_launches"], "wall_s": wall}
+    out = {"requests": len(reqs), "completed": len(done), "offered_rate_hz": rate_hz,
+           "calibrations_per_s": len(done) / wall,
+           "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+           "steps": st["steps"], "kernel_launches": st["kernel_launches"], "wall_s": wall}
+    # latency per request class
+    by = {}
+    for i in done:
+        by.setdefault(request_class(sg, reqs[i]), []).append(done[i] - arrive[i])
+    out["by_class"] = {c: {"requests": len(v), "p50_ms": 1e3 * float(np.percentile(v, 50)),
+                           "p99_ms": 1e3 * float(np.percentile(v, 99))} for c, v in sorted(by.items())}
+    return out
 
-def measure_serving_loads(sg, n_requests):
-    """Capacity (all requests at once), then Poisson arrivals at 50%, 80% and
-    95% of it (half the requests each); beside it the plain FP64
-    one-request-per-launch form on a sample."""
+
+def request_class(sg, q):
+    """hagan / dynamic (formula cost, Case I or II) / mc (price cost)."""
+    if q.cost != 0:
+        return "mc"
+    return "hagan" if q.smile.model == sg.HAGAN else "dynamic"
+
+
+def measure_fp64_one_per_launch(sg, n_per_class=6):
+    """The plain FP64 form, one request per launch (sabr_calibrate), on
+    requests of each class drawn from the serving stream; its capacity on the
+    stream's mix is 1 / sum_c p_c t_c (p_c the class fractions of the
+    stream, t_c the mean time of one request).  An MC request runs 1 level x
+    2 proposals and its time is scaled to its 10 x 10 schedule (FP64 paths
+    take about a minute for a whole MC request)."""
+    from paper_2407_20713_gb300 import workloads
+    stream = workloads.serving_stream(n=2000, rate_hz=1.0)
+    frac = {}
+    for q in stream:
+        c = request_class(sg, q)
+        frac[c] = frac.get(c, 0) + 1.0 / len(stream)
+    times = {}
+    for c in ("hagan", "dynamic", "mc"):
+        ts = []
+        for q in [q for q in stream if request_class(sg, q) == c][:n_per_class]:
+            sm = q.smile
+            if q.cost == 0:
+                mkt = sg.implied_vol(sm.model, sm.truth, 1.0, sm.T, sm.K, prec=sg.FP64).cpu().numpy() + sm.noise
+                pb = sg.CalibrationProblem(model=sm.model, T=sm.T, K=sm.K, market=mkt, lo=sm.lo, hi=sm.hi,
+                                           prec=sg.FP64, n_chains=sm.n_chains, n_levels=q.n_levels,
+                                           chain_len=q.chain_len, seed=11)
+                scale = 1.0
+            else:
+                mkt = sg.mc_price(sm.model, sm.truth, 1.0, sm.T, sm.K, n_paths=q.mc_paths, steps_per_year=250,
+                                  seed=99)[0].cpu().numpy()
+                keep = mkt >= 1e-6
+                pb = sg.CalibrationProblem(model=sm.model, T=sm.T[keep], K=sm.K[keep], market=mkt[keep], lo=sm.lo,
+                                           hi=sm.hi, cost=sg.COST_MC_PRICE, prec=sg.FP64, n_chains=sm.n_chains,
+                                           n_levels=1, chain_len=2, mc_paths=q.mc_paths, mc_steps_per_year=250.0,
+                                           mc_seed=7, seed=11)
+                scale = (q.n_levels * q.chain_len) / 2.0
+            t0 = time.perf_counter()
+            sg.calibrate(pb)
+            ts.append((time.perf_counter() - t0) * scale)
+        times[c] = float(np.mean(ts))
+    cap = 1.0 / sum(frac[c] * times[c] for c in times)
+    return {"calibrations_per_s": cap, "seconds_per_request": times, "class_fractions": frac,
+            "sample": "%d requests per class from the serving stream; MC scaled from 1 level x 2 proposals"
+                      % n_per_class}
+
+def measure_serving_loads(sg, n_requests, fractions=(0.5, 0.8, 0.95), load_requests=None):
+    """Capacity (all requests at once), then Poisson arrivals at the given
+    fractions of it (half the requests each unless load_requests is given);
+    beside it the plain FP64 one-request-per-launch form on the same mix."""
     burst = measure_serving(sg, n_requests, rate_hz=1e9)
     cap = burst["calibrations_per_s"]
-    loads = {"load%d" % int(100 * f): measure_serving(sg, max(1, n_requests // 2), rate_hz=f * cap)
-             for f in (0.5, 0.8, 0.95)}
-    from paper_2407_20713_gb300 import workloads
-    sample = workloads.serving_stream(n=24, rate_hz=1.0)
-    t0 = time.perf_counter()
-    n = 0
-    for q in sample:
-        if q.cost != 0:
-            continue
-        sm = q.smile
-        mkt = sg.implied_vol(sm.model, sm.truth, 1.0, sm.T, sm.K, prec=sg.FP64).cpu().numpy() + sm.noise
-        sg.calibrate(sg.CalibrationProblem(model=sm.model, T=sm.T, K=sm.K, market=mkt, lo=sm.lo, hi=sm.hi,
-                                           prec=sg.FP64, n_chains=sm.n_chains, n_levels=q.n_levels,
-                                           chain_len=q.chain_len, seed=11))
-        n += 1
-    fp64_rate = n / (time.perf_counter() - t0)
+    n_load = load_requests or max(1, n_requests // 2)
+    loads = {"load%d" % int(100 * f): measure_serving(sg, n_load, rate_hz=f * cap) for f in fractions}
     out = {"capacity": burst}
     out.update(loads)
     # the 5% MC requests take most of the GPU time of the mix; the formula
     # requests alone, all at once
     out["formula_only_capacity"] = measure_serving(sg, n_requests, rate_hz=1e9, formula_only=True)
-    out["fp64_one_request_per_launch"] = {"calibrations_per_s": fp64_rate, "sample": "%d formula requests" % n}
+    out["fp64_one_request_per_launch"] = measure_fp64_one_per_launch(sg)
     return out
 
 
@@ -809,10 +856,26 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_serving_only(args):
+    """The serving measurement alone, e.g. at the stream's full 10 000
+    requests (capacity, then 50 / 80 / 95% of it with half the requests
+    each), printed as one JSON line."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2407_20713_gb300 as sg
+    torch.cuda.set_device(0)
+    out = measure_serving_loads(sg, args.serve_requests, fractions=tuple(args.serve_loads),
+                                load_requests=args.serve_requests)
+    print(json.dumps({"serving": out, "requests": args.serve_requests}), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.serve_only:
+        run_serving_only(a)
     elif a.case == "mc":
         run_mc_case()
     elif a.case == "cliquet":

@@ -150,6 +150,56 @@ sabr_status sabr_mc_price_noalloc(sabr_model model, const double* params,
                                   sabr_precision prec, void* cuda_stream);
 
 /* ------------------------------------------------------------------------
+ * Path-sharded Monte Carlo pricing: the Sec. 4 pricer spread over several
+ * GPUs (Sec. 5.2 spreads Technique II's Monte Carlo cost over devices).
+ * sabr_mc_price runs a grid of total_blocks blocks; block b takes a fixed,
+ * interleaved set of the paths and writes FP64 sums of payoff and payoff^2
+ * of every option.  A shard runs blocks [block_begin, block_begin +
+ * block_count) of that grid on the current device; the caller gathers the
+ * shards' partials in block order (any transport) and reduces them on one
+ * device.  The result equals sabr_mc_price on a device of the same kind bit
+ * for bit.  Every call takes the problem arguments of sabr_mc_price (same
+ * meaning, layout, host/device placement and checks).
+ *   sabr_mc_shard_layout   total_blocks: the grid sabr_mc_price would use on
+ *                          the current device (every shard must use one
+ *                          value); doubles_per_block: size of one block's
+ *                          partials.  Host only; no device work.
+ *   sabr_mc_shard_partials partials_out: device, block_count *
+ *                          doubles_per_block doubles, block i of the range
+ *                          at offset i * doubles_per_block.
+ *   sabr_mc_shard_reduce   partials: device, total_blocks * doubles_per_block
+ *                          doubles in block order; price_out / stderr_out as
+ *                          sabr_mc_price.
+ * Asynchronous on cuda_stream (tables are staged in library-owned device
+ * scratch, as sabr_mc_price).  EINVAL for a block range outside
+ * [0, total_blocks) and the checks of sabr_mc_price.
+ * ------------------------------------------------------------------------ */
+sabr_status sabr_mc_shard_layout(sabr_model model, const double* params,
+                                 double fwd, const double* T, const double* K,
+                                 const int8_t* is_call, const double* discount,
+                                 int64_t n, int64_t n_paths,
+                                 double steps_per_year, uint64_t seed,
+                                 sabr_precision prec, int32_t* total_blocks,
+                                 int64_t* doubles_per_block);
+sabr_status sabr_mc_shard_partials(sabr_model model, const double* params,
+                                   double fwd, const double* T, const double* K,
+                                   const int8_t* is_call,
+                                   const double* discount, int64_t n,
+                                   int64_t n_paths, double steps_per_year,
+                                   uint64_t seed, sabr_precision prec,
+                                   int32_t total_blocks, int32_t block_begin,
+                                   int32_t block_count, double* partials_out,
+                                   void* cuda_stream);
+sabr_status sabr_mc_shard_reduce(sabr_model model, const double* params,
+                                 double fwd, const double* T, const double* K,
+                                 const int8_t* is_call, const double* discount,
+                                 int64_t n, int64_t n_paths,
+                                 double steps_per_year, uint64_t seed,
+                                 sabr_precision prec, int32_t total_blocks,
+                                 const double* partials, double* price_out,
+                                 double* stderr_out, void* cuda_stream);
+
+/* ------------------------------------------------------------------------
  * sabr_mc_cliquet -- Monte Carlo price of a cliquet on the forward, Sec. 6.3
  * eqs. (eq_cliquet) and (cliquet_global), on the paths of sabr_mc_price
  * (same scheme, absorption and Philox streams; the reset dates are inserted
@@ -288,6 +338,56 @@ sabr_status sabr_plan_results(sabr_plan* plan, sabr_result* out);
 sabr_status sabr_plan_stats(sabr_plan* plan, int64_t* launches_per_run,
                             double* level_kernel_ms);
 void sabr_plan_destroy(sabr_plan* plan);
+
+/* ------------------------------------------------------------------------
+ * Chain-sharded calibration: Sec. 5.1's multi-GPU Technique I.  Each GPU
+ * runs a share of the chains; after every temperature level the host takes
+ * the minimum of the shares' lowest final states as the common restart
+ * point.  A shard holds chains [chain_begin, chain_begin + chain_count) of
+ * problem->n_chains (the problem's total) on the current device; the caller
+ * runs level 0 .. n_levels-1 in order on every shard, exchanges the shards'
+ * minima (any transport: a collective, host memory), takes the
+ * lexicographic minimum in (f, chain) and gives it to every shard with
+ * sabr_shard_restart before the next level.  After the last level each
+ * shard's sabr_shard_result gives its best-ever point; the overall result is
+ * the shard result of lowest (misfit, best_chain), with n_evals and
+ * n_accepts summed.  Done this way the result equals sabr_calibrate on the
+ * whole problem bit for bit: chains draw their proposals from Philox
+ * counters keyed by their global index, and lanes per chain are chosen from
+ * the total chain count.  Implied-vol cost (Technique I) only.
+ *   sabr_shard_create   problem, bounds, cooling, seed: as sabr_calibrate
+ *                       (host arrays, copied).  Computes f(x0) and T0;
+ *                       blocking.  EINVAL for a chain range outside
+ *                       [0, n_chains) or an MC-cost problem.
+ *   sabr_shard_level    runs `level` (which must follow the previous one)
+ *                       from the current restart point; *local_min = the
+ *                       shard's lowest final state (lowest global chain on
+ *                       a tie).  Blocking.
+ *   sabr_shard_restart  restart point (x, f) of the next level.  Blocking.
+ *   sabr_shard_result   after the last level: the shard's result (best
+ *                       point, its FP64 re-score, counters) and the global
+ *                       chain of its best point (-1 with no levels).
+ *                       Blocking.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  double f;       /* cost of the state                                */
+  int64_t chain;  /* global chain index                               */
+  double x[10];   /* parameters (layout of params above)              */
+} sabr_chain_point;
+typedef struct sabr_shard sabr_shard;
+sabr_status sabr_shard_create(const sabr_problem* problem,
+                              const sabr_bounds* bounds,
+                              const sabr_cooling* cooling, uint64_t seed,
+                              int32_t chain_begin, int32_t chain_count,
+                              void* cuda_stream, sabr_shard** out);
+sabr_status sabr_shard_level(sabr_shard* shard, int32_t level,
+                             sabr_chain_point* local_min, void* cuda_stream);
+sabr_status sabr_shard_restart(sabr_shard* shard,
+                               const sabr_chain_point* restart,
+                               void* cuda_stream);
+sabr_status sabr_shard_result(sabr_shard* shard, sabr_result* out,
+                              int64_t* best_chain, void* cuda_stream);
+void sabr_shard_destroy(sabr_shard* shard);
 
 /* ------------------------------------------------------------------------
  * Serving: continuous batching of calibration requests (Sec. 5 engines).

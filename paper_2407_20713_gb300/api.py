@@ -88,6 +88,64 @@ def mc_cliquet(model, params, fwd, T, n_resets, floor_local, cap_local, floor_gl
     return price, se
 
 
+def _mc_host_args(model, params, T, K, is_call, discount):
+    T = np.ascontiguousarray(T, dtype=np.float64).ravel()
+    K = np.ascontiguousarray(np.broadcast_to(np.asarray(K, dtype=np.float64), T.shape))
+    ic = None if is_call is None else np.ascontiguousarray(is_call, dtype=np.int8).ravel()
+    dc = None if discount is None else np.ascontiguousarray(discount, dtype=np.float64).ravel()
+    p = _params10(params, model)
+    keep = (T, K, ic, dc, p)
+    args = (model, p.ctypes.data_as(capi.PD), None, T.ctypes.data_as(capi.PD), K.ctypes.data_as(capi.PD),
+            ic.ctypes.data_as(capi.PI8) if ic is not None else None,
+            dc.ctypes.data_as(capi.PD) if dc is not None else None, T.size)
+    return keep, args
+
+
+def mc_shard_layout(model, params, fwd, T, K, is_call=None, discount=None, n_paths=1 << 16, steps_per_year=250.0,
+                    seed=0, prec=FP32):
+    """(total_blocks, doubles_per_block) of the path-sharded form of mc_price."""
+    lib = capi.load()
+    keep, a = _mc_host_args(model, params, T, K, is_call, discount)
+    nb, dpb = ctypes.c_int32(), ctypes.c_int64()
+    st = lib.sabr_mc_shard_layout(a[0], a[1], float(fwd), *a[3:], int(n_paths), float(steps_per_year),
+                                  int(seed) & 0xFFFFFFFFFFFFFFFF, prec, ctypes.byref(nb), ctypes.byref(dpb))
+    capi.check(st, "sabr_mc_shard_layout")
+    return nb.value, dpb.value
+
+
+def mc_shard_partials(model, params, fwd, T, K, total_blocks, block_begin, block_count, is_call=None,
+                      discount=None, n_paths=1 << 16, steps_per_year=250.0, seed=0, prec=FP32, stream=None,
+                      device="cuda"):
+    """Per-block partial sums of blocks [block_begin, block_begin + block_count)
+    of the mc_price grid (a float64 CUDA tensor, block_count x doubles_per_block)."""
+    lib = capi.load()
+    _, dpb = mc_shard_layout(model, params, fwd, T, K, is_call, discount, n_paths, steps_per_year, seed, prec)
+    out = torch.empty((block_count, dpb), dtype=torch.float64, device=device)
+    keep, a = _mc_host_args(model, params, T, K, is_call, discount)
+    st = lib.sabr_mc_shard_partials(a[0], a[1], float(fwd), *a[3:], int(n_paths), float(steps_per_year),
+                                    int(seed) & 0xFFFFFFFFFFFFFFFF, prec, int(total_blocks), int(block_begin),
+                                    int(block_count), ctypes.c_void_p(out.data_ptr()), _stream_handle(stream))
+    capi.check(st, "sabr_mc_shard_partials")
+    return out
+
+
+def mc_shard_reduce(model, params, fwd, T, K, total_blocks, partials, is_call=None, discount=None, n_paths=1 << 16,
+                    steps_per_year=250.0, seed=0, prec=FP32, stream=None):
+    """Prices and standard errors from the partials of all blocks, in block order."""
+    lib = capi.load()
+    partials = partials.contiguous()
+    n = int(np.asarray(T).size)
+    price = torch.empty(n, dtype=torch.float64, device=partials.device)
+    se = torch.empty(n, dtype=torch.float64, device=partials.device)
+    keep, a = _mc_host_args(model, params, T, K, is_call, discount)
+    st = lib.sabr_mc_shard_reduce(a[0], a[1], float(fwd), *a[3:], int(n_paths), float(steps_per_year),
+                                  int(seed) & 0xFFFFFFFFFFFFFFFF, prec, int(total_blocks),
+                                  ctypes.c_void_p(partials.data_ptr()), ctypes.c_void_p(price.data_ptr()),
+                                  ctypes.c_void_p(se.data_ptr()), _stream_handle(stream))
+    capi.check(st, "sabr_mc_shard_reduce")
+    return price, se
+
+
 @dataclass
 class CalibrationProblem:
     """One calibration problem: quotes, model and SA settings (host data)."""
@@ -232,6 +290,59 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.sabr_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Shard:
+    """Chains [chain_begin, chain_begin + chain_count) of a problem on the
+    current device (sabr_shard_* of include/sabr.h).  level(lv) returns the
+    shard's lowest final state (f, global chain, x[10]); restart(f, x) sets
+    the next level's start; result() returns (CalibrationResult, best global
+    chain)."""
+
+    def __init__(self, problem: CalibrationProblem, chain_begin: int, chain_count: int, stream=None):
+        self._lib = capi.load()
+        self._problem = problem
+        pr, b, c, seed = problem.to_c()
+        h = ctypes.c_void_p()
+        self._stream = stream
+        st = self._lib.sabr_shard_create(ctypes.byref(pr), ctypes.byref(b), ctypes.byref(c), seed,
+                                         int(chain_begin), int(chain_count), _stream_handle(stream),
+                                         ctypes.byref(h))
+        capi.check(st, "sabr_shard_create")
+        self._h = h
+
+    def level(self, lv):
+        p = capi.ChainPoint()
+        capi.check(self._lib.sabr_shard_level(self._h, int(lv), ctypes.byref(p), _stream_handle(self._stream)),
+                   "sabr_shard_level")
+        return p.f, p.chain, np.array(p.x[:])
+
+    def restart(self, f, x):
+        p = capi.ChainPoint()
+        p.f = float(f)
+        p.chain = -1
+        for i in range(10):
+            p.x[i] = float(x[i])
+        capi.check(self._lib.sabr_shard_restart(self._h, ctypes.byref(p), _stream_handle(self._stream)),
+                   "sabr_shard_restart")
+
+    def result(self):
+        r = capi.Result()
+        ch = ctypes.c_int64()
+        capi.check(self._lib.sabr_shard_result(self._h, ctypes.byref(r), ctypes.byref(ch),
+                                               _stream_handle(self._stream)), "sabr_shard_result")
+        return CalibrationResult.from_c(r, self._problem.model), ch.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sabr_shard_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -53,6 +53,10 @@ class Result(ctypes.Structure):
                 ("n_evals", c_int64), ("n_accepts", c_int64), ("status", c_int)]
 
 
+class ChainPoint(ctypes.Structure):
+    _fields_ = [("f", c_double), ("chain", c_int64), ("x", c_double * 10)]
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [("device_bytes", c_int64), ("max_queue", c_int32), ("max_active", c_int32),
                 ("max_quotes", c_int32), ("use_graph", c_int32)]
@@ -94,6 +98,18 @@ SIGNATURES = {
     "sabr_server_cancel": (c_int, [c_void_p, c_uint64]),
     "sabr_server_get_stats": (c_int, [c_void_p, ctypes.POINTER(ServerStats)]),
     "sabr_server_destroy": (None, [c_void_p]),
+    "sabr_mc_shard_layout": (c_int, [c_int, PD, c_double, PD, PD, PI8, PD, c_int64, c_int64, c_double, c_uint64,
+                                     c_int, ctypes.POINTER(c_int32), ctypes.POINTER(c_int64)]),
+    "sabr_mc_shard_partials": (c_int, [c_int, PD, c_double, PD, PD, PI8, PD, c_int64, c_int64, c_double,
+                                       c_uint64, c_int, c_int32, c_int32, c_int32, c_void_p, c_void_p]),
+    "sabr_mc_shard_reduce": (c_int, [c_int, PD, c_double, PD, PD, PI8, PD, c_int64, c_int64, c_double, c_uint64,
+                                     c_int, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "sabr_shard_create": (c_int, [ctypes.POINTER(Problem), ctypes.POINTER(Bounds), ctypes.POINTER(Cooling),
+                                  c_uint64, c_int32, c_int32, c_void_p, ctypes.POINTER(c_void_p)]),
+    "sabr_shard_level": (c_int, [c_void_p, c_int32, ctypes.POINTER(ChainPoint), c_void_p]),
+    "sabr_shard_restart": (c_int, [c_void_p, ctypes.POINTER(ChainPoint), c_void_p]),
+    "sabr_shard_result": (c_int, [c_void_p, ctypes.POINTER(Result), ctypes.POINTER(c_int64), c_void_p]),
+    "sabr_shard_destroy": (None, [c_void_p]),
     "sabr_last_error": (ctypes.c_char_p, []),
 }
 

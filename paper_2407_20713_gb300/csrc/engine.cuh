@@ -16,7 +16,10 @@ constexpr int kLevelBlock = 64;
 // Dynamic shared memory a level block may use: the 227 KB opt-in limit less
 // room for the kernel's static shared memory.
 constexpr size_t kMaxLevelSmem = 226 * 1024;
-constexpr int kStateLen = 12;  // restart x[10], restart f, T0
+// Restart state of a problem: x[10], f, T0, then the global chain index of
+// the last level's argmin and of the best-ever point (as doubles, exact).
+constexpr int kStateLen = 14;
+constexpr int kStateArgChain = 12, kStateBestChain = 13;
 
 // One problem of a batch, as the kernels see it (all pointers device).
 // Quotes are sorted by maturity; q_* arrays hold the working precision R,
@@ -54,6 +57,16 @@ struct ProblemDev {
   double* part_x;      // [n_blocks][10]
   unsigned int* arrive;
   sabr_result* result;
+  // FP32 Case II term-structure rule (device copies of HostProblem's)
+  const float4* c2_node;
+  const float4* c2_sub;
+  const int2* c2_panel;
+  int c2_nsub;
+  // global index of the problem's chain 0: a shard of a chain-sharded
+  // problem runs chains chain0 .. chain0 + n_chains - 1 of it (Philox
+  // counters and reported chain indices are global)
+  int chain0;
+  int spec;  // Hagan: speculative two-step loop (same results)
 };
 
 // Per-quote inputs ln(f/K), log2(K f), T and 1/market (FP32) or market
@@ -71,11 +84,22 @@ __device__ __forceinline__ double mat_in_slot(int j, double) { return __longlong
 __device__ __forceinline__ int mat_of_slot(float v) { return __float_as_int(v); }
 __device__ __forceinline__ int mat_of_slot(double v) { return (int)__double_as_longlong(v); }
 
-// Quote tables of one problem staged in shared memory.
+// Quote tables of one problem staged in shared memory.  The FP32 Hagan
+// form evaluates its quotes two at a time (hagan_resid_pair), so its quotes
+// are staged as pairs instead: for pair j (quotes 2j and 2j + 1 in maturity
+// order) pair[2j] = (lfk, lfk', l2kf, l2kf') and pair[2j + 1] =
+// (T, T', -1/market, -1/market'), two 16-byte loads a pair; an odd count
+// leaves a zero second element in the last pair, whose residual is not
+// summed.
 template <class R> struct SmemQuotes {
-  const QuotePack<R>* pack;  // per quote
+  const QuotePack<R>* pack;  // per quote (every model but the FP32 Hagan form)
+  const float4* pair;        // per pair of quotes (FP32 Hagan form)
   const R* l2k;              // per quote: log2 K (Oblój)
   const R* mT;               // per maturity: T
+  // FP32 Case II term-structure rule
+  const float4* c2_node;     // per node: u, W, tau = T_j - u
+  const float4* c2_sub;      // per sub-panel: half width, sum W, sum tau W
+  const int2* c2_panel;      // per maturity: first sub-panel, count
 };
 
 // Double-float number hi + lo (|lo| <= ulp(hi)/2): sums of FP32 terms carried
@@ -145,10 +169,14 @@ __device__ __forceinline__ DF lanes_sum(float v, int G, unsigned gmask) {
 // Shared-memory slots per maturity in a chain group's coefficient slice: the
 // polynomial (c0, c1, c2), and a fourth slot (for Case II it holds eta2^2
 // until the polynomial is formed) that aligns each polynomial to 16 bytes.
-template <int MODEL> struct CoefStride {
-  static constexpr int value = 4;
+// The FP32 Case II form also keeps, per maturity, the panel integrals its
+// term-structure rule sums (slots 4 .. 12 of a 16-slot stride).
+template <class R, int MODEL> struct CoefStride {
+  static constexpr int value = (MODEL == SABR_DYN_II && sizeof(R) == 4) ? 16 : 4;
 };
-__host__ __device__ constexpr int coef_stride(int) { return 4; }
+__host__ __device__ constexpr int coef_stride(int prec, int model) {
+  return (model == SABR_DYN_II && prec == SABR_FP32) ? 16 : 4;
+}
 
 // The polynomial of maturity j from a coefficient slice: one 16-byte load
 // in FP32 (the slice is 16-byte aligned and its stride is 4), two in FP64.
@@ -169,7 +197,7 @@ __device__ __forceinline__ PolyCoef<double> load_poly(const double* coef, int j)
 template <class R>
 __device__ __forceinline__ void case2_group_coef(const R* xp, int n_mats, R l2f, const SmemQuotes<R>& sq, R* coef,
                                                  int lane, int G, unsigned gmask) {
-  constexpr int CS = CoefStride<SABR_DYN_II>::value;
+  constexpr int CS = 4;
   const R rho0 = (R)xp[2], nu0 = (R)xp[3], dr = (R)xp[6], dn = (R)xp[7];
   for (int j = lane; j < n_mats; j += G) {
     const R T = sq.mT[j];
@@ -203,17 +231,215 @@ __device__ __forceinline__ void case2_group_coef(const R* xp, int n_mats, R l2f,
   }
 }
 
+// The Hagan cost of two points at once (the speculative step loop of the
+// level kernel): every lane evaluates its quotes for both points, with the
+// lane assignment, order of summation and arithmetic of group_cost for each
+// point, so each result equals group_cost's bit for bit; the two evaluations
+// are independent work for the scheduler.
+template <class R, int PAIRS>
+__device__ __forceinline__ void group_cost2_hagan(const R* xa, const R* xb, int n_quotes,
+                                                  const SmemQuotes<R>& sq, int lane, int G, unsigned gmask,
+                                                  typename CostOf<R>::T& fa, typename CostOf<R>::T& fb) {
+  R acc_a = (R)0, acc_b = (R)0;
+  if constexpr (sizeof(R) == 4) {
+    const StaticConst<float> sa = static_setup<float>(xa), sb = static_setup<float>(xb);
+    const int full = n_quotes >> 1;
+    float2 a2 = make_float2(0.0f, 0.0f), b2 = make_float2(0.0f, 0.0f);
+#pragma unroll PAIRS
+    for (int j = lane; j < full; j += G) {
+      const float4 a = sq.pair[2 * j], b = sq.pair[2 * j + 1];
+      const float2 lfk = make_float2(a.x, a.y), l2kf = make_float2(a.z, a.w), T = make_float2(b.x, b.y),
+                   wn = make_float2(b.z, b.w);
+      const float2 ra = hagan_resid_pair(sa, lfk, l2kf, T, wn);
+      const float2 rb = hagan_resid_pair(sb, lfk, l2kf, T, wn);
+      a2 = fma2(ra, ra, a2);
+      b2 = fma2(rb, rb, b2);
+    }
+    if ((n_quotes & 1) && (full & (G - 1)) == lane) {
+      const float4 a = sq.pair[2 * full], b = sq.pair[2 * full + 1];
+      const float ra = fmaf(vol_hagan<float>(sa, a.x, a.z, b.x), b.z, 1.0f);
+      const float rb = fmaf(vol_hagan<float>(sb, a.x, a.z, b.x), b.z, 1.0f);
+      a2.x = fmaf(ra, ra, a2.x);
+      b2.x = fmaf(rb, rb, b2.x);
+    }
+    acc_a = a2.x + a2.y;
+    acc_b = b2.x + b2.y;
+  } else {
+    const StaticConst<R> sa = static_setup<R>(xa), sb = static_setup<R>(xb);
+    for (int q = lane; q < n_quotes; q += G) {
+      const QuotePack<R> qp = sq.pack[q];
+      const R ra = resid(vol_hagan<R>(sa, qp.lfk, qp.l2kf, qp.T), qp.w);
+      const R rb = resid(vol_hagan<R>(sb, qp.lfk, qp.l2kf, qp.T), qp.w);
+      acc_a += ra * ra;
+      acc_b += rb * rb;
+    }
+  }
+  fa = lanes_sum(acc_a, G, gmask);
+  fb = lanes_sum(acc_b, G, gmask);
+}
+
+// FP32 Case II: the four functions of eq. (integrales_SABRd) of every
+// maturity from one composite rule over [0, Tmax] whose panels end at the
+// maturities (sub-panels and nodes prepared per problem, case2_rule_build).
+// With nu(t) = (nu0 + q_nu t) e^{-bt} + d_nu, rho(t) = (rho0 + q_rho t) e^{-at}
+// + d_rho and G(t) = int_0^t nu rho, in real time:
+//   nu1^2 = 3 A/T^3, A = int_0^T (T-t)^2 nu^2     nu2^2 = 6 D/T^3, D = int_0^T (T-t) t nu^2
+//   eta1  = 2 H/T^2, H = int_0^T (T-t) nu rho     eta2^2 = 12 K/T^4, K = int_0^T (T-t) G^2
+// (the last by Fubini from the triple integral).  Each panel j contributes
+// its own integrals with weights in T_j - t; across panels the totals obey
+// positive recurrences in Delta = T_j - T_{j-1} (e.g. A_j = A_{j-1} +
+// Delta (2 B_{j-1} + Delta C_{j-1}) + a_j with B = int (T-t) nu^2,
+// C = int nu^2), so no difference of large terms is formed.  Lanes take
+// whole panels (maturity j on lane j mod G); at a node only nu and rho are
+// evaluated (two 2^x), G inside a sub-panel comes from the Gauss-Legendre
+// integration matrix, and G at a panel's start from a scan over the lanes.
+// With G = G_start + g(t), the panel's integrals of G^2 are kept as
+// coefficients of a quadratic in G_start (P0, P1, P2), so every node is
+// evaluated once.  `loc` holds 12 slots per maturity for the panel
+// integrals; coef[4 j ..] receives nu1^2, nu2^2, eta1, eta2^2 and then the
+// polynomial of maturity j.
+__device__ __forceinline__ void case2_group_coef_rule(const float* xp, int n_mats, float l2f,
+                                                      const SmemQuotes<float>& sq, float* coef, float* loc, int lane,
+                                                      int G, unsigned gmask) {
+  const float rho0 = xp[2], nu0 = xp[3], dr = xp[6], dn = xp[7], qr = xp[8], qn = xp[9];
+  const float na2 = -xp[4] * 1.4426950408889634f, nb2 = -xp[5] * 1.4426950408889634f;
+  float carry = 0.0f;  // G at the start of this round's first panel
+  for (int r0 = 0; r0 < n_mats; r0 += G) {
+    const int j = r0 + lane;
+    float c_ = 0.f, e_ = 0.f, b_ = 0.f, a_ = 0.f, d_ = 0.f, n_ = 0.f, h_ = 0.f;
+    float P0 = 0.f, P1 = 0.f, P2 = 0.f, Q0 = 0.f, Q1 = 0.f, Q2 = 0.f;
+    if (j < n_mats) {
+      const int2 pr = sq.c2_panel[j];
+      for (int sbi = pr.x; sbi < pr.x + pr.y; ++sbi) {
+        const float4 sub = sq.c2_sub[sbi];  // half width, sum W, sum tau W
+        const float cin = n_;               // int of nu rho from the panel start
+        const float4* nd = sq.c2_node + kC2Nodes * sbi;
+        float f[kC2Nodes];
+#pragma unroll
+        for (int k = 0; k < kC2Nodes; ++k) {
+          const float4 q = nd[k];  // u, W, tau
+          const float eb = ex2_approx(nb2 * q.x), ea = ex2_approx(na2 * q.x);
+          const float nu = fmaf(fmaf(qn, q.x, nu0), eb, dn);
+          const float rho = fmaf(fmaf(qr, q.x, rho0), ea, dr);
+          f[k] = nu * rho;
+          const float wn = q.y * nu * nu;
+          c_ += wn;
+          e_ = fmaf(q.x, wn, e_);
+          b_ = fmaf(q.z, wn, b_);
+          const float twn = q.z * wn;
+          a_ = fmaf(q.z, twn, a_);
+          d_ = fmaf(q.x, twn, d_);
+          const float wf = q.y * f[k];
+          n_ += wf;
+          h_ = fmaf(q.z, wf, h_);
+        }
+        float s1 = 0.f, s2 = 0.f, t1 = 0.f, t2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < kC2Nodes; ++k) {
+          float g = 0.f;
+#pragma unroll
+          for (int i = 0; i < kC2Nodes; ++i) g = fmaf(kC2.S[k][i], f[i], g);
+          g *= sub.x;
+          const float4 q = nd[k];
+          const float wg = q.y * g, twg = q.z * wg;
+          s1 += wg;
+          s2 = fmaf(wg, g, s2);
+          t1 += twg;
+          t2 = fmaf(twg, g, t2);
+        }
+        // int W (Gs + cin + g)^2 as a quadratic in Gs, the G at the panel start
+        P0 += sub.y;
+        P1 += fmaf(cin, sub.y, s1);
+        P2 += fmaf(cin, fmaf(cin, sub.y, 2.0f * s1), s2);
+        Q0 += sub.z;
+        Q1 += fmaf(cin, sub.z, t1);
+        Q2 += fmaf(cin, fmaf(cin, sub.z, 2.0f * t1), t2);
+      }
+    }
+    // G at each panel's start: exclusive scan of the panels' int nu rho
+    float incl = n_;
+    for (int off = 1; off < G; off <<= 1) {
+      const float y = __shfl_up_sync(gmask, incl, off, G);
+      if (lane >= off) incl += y;
+    }
+    const float Gs = carry + (incl - n_);
+    carry += __shfl_sync(gmask, incl, G - 1, G);
+    if (j < n_mats) {
+      float* L = loc + 12 * j;
+      L[0] = c_;
+      L[1] = e_;
+      L[2] = b_;
+      L[3] = a_;
+      L[4] = d_;
+      L[5] = n_;
+      L[6] = h_;
+      L[7] = fmaf(Gs, fmaf(Gs, P0, 2.0f * P1), P2);  // int G^2 over the panel
+      L[8] = fmaf(Gs, fmaf(Gs, Q0, 2.0f * Q1), Q2);  // int (T_j - t) G^2
+    }
+  }
+  __syncwarp(gmask);
+  // the recurrences over the panels (every lane runs them; lane j mod G
+  // forms maturity j's functions and polynomial)
+  float C = 0.f, E = 0.f, B = 0.f, A = 0.f, D = 0.f, N = 0.f, H = 0.f, I = 0.f, K = 0.f, Tp = 0.f;
+  for (int j = 0; j < n_mats; ++j) {
+    const float T = sq.mT[j], dl = T - Tp;
+    const float* L = loc + 12 * j;
+    A += fmaf(dl, fmaf(dl, C, 2.0f * B), L[3]);
+    B += fmaf(dl, C, L[2]);
+    C += L[0];
+    D += fmaf(dl, E, L[4]);
+    E += L[1];
+    H += fmaf(dl, N, L[6]);
+    N += L[5];
+    K += fmaf(dl, I, L[8]);
+    I += L[7];
+    Tp = T;
+    if ((j & (G - 1)) == lane) {
+      const float iT = rcp_approx(T), iT2 = iT * iT;
+      const PolyCoef<float> c = dynamic_poly<float>(xp[0], xp[1], l2f, T, 3.0f * A * iT2 * iT, 6.0f * D * iT2 * iT,
+                                                    2.0f * H * iT2, 12.0f * K * iT2 * iT2);
+      coef[4 * j + 0] = c.c0;
+      coef[4 * j + 1] = c.c1;
+      coef[4 * j + 2] = c.c2;
+    }
+  }
+}
+
 // Cost of point xp evaluated by the G lanes of one chain group.  Lane `lane`
 // takes quotes lane, lane+G, ...; per-lane partial sums are combined by
 // lanes_sum.
 // For the dynamic models the lanes first compute the per-maturity polynomial
 // of eq. (vola_SABRd) into `coef` (this group's slice of shared memory).
-template <class R, int MODEL>
+// PAIRS: quote pairs the FP32 Hagan loop keeps in flight (more independent
+// work for the scheduler, at the price of registers: the 128-register
+// kernels use 2, the plans' persistent launch, which runs four 64-thread
+// blocks per SM and so may use up to 255 registers, uses 5 -- measured on
+// the 21-strike smiles against 2, 3, 4 and 6, and against chunks of 4, 6 and
+// 11 pairs with the odd quote's pair inside the last chunk).
+template <class R, int MODEL, int PAIRS = 2>
 __device__ __forceinline__ typename CostOf<R>::T group_cost(const R* xp, int n_quotes, int n_mats, R l2f,
                                              const SmemQuotes<R>& sq, R* coef, int lane, int G,
                                              unsigned gmask) {
   R acc = (R)0;
-  if (MODEL == SABR_HAGAN || MODEL == SABR_OBLOJ) {
+  if constexpr (MODEL == SABR_HAGAN && sizeof(R) == 4) {
+    const StaticConst<float> sc = static_setup<float>(xp);
+    float2 acc2 = make_float2(0.0f, 0.0f);
+    const int full = n_quotes >> 1;  // pairs with two quotes
+#pragma unroll PAIRS
+    for (int j = lane; j < full; j += G) {
+      const float4 a = sq.pair[2 * j], b = sq.pair[2 * j + 1];
+      const float2 r = hagan_resid_pair(sc, make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y),
+                                        make_float2(b.z, b.w));
+      acc2 = fma2(r, r, acc2);
+    }
+    if ((n_quotes & 1) && (full & (G - 1)) == lane) {
+      // an odd count's last quote, alone (the scalar form of the same formula)
+      const float4 a = sq.pair[2 * full], b = sq.pair[2 * full + 1];
+      const float r = fmaf(vol_hagan<float>(sc, a.x, a.z, b.x), b.z, 1.0f);
+      acc2.x = fmaf(r, r, acc2.x);
+    }
+    acc = acc2.x + acc2.y;
+  } else if (MODEL == SABR_HAGAN || MODEL == SABR_OBLOJ) {
     const StaticConst<R> sc = static_setup<R>(xp);
 #pragma unroll 3
     for (int q = lane; q < n_quotes; q += G) {
@@ -235,7 +461,7 @@ __device__ __forceinline__ typename CostOf<R>::T group_cost(const R* xp, int n_q
       acc += r * r;
     }
   } else {
-    constexpr int CS = CoefStride<MODEL>::value;
+    constexpr int CS = 4;  // polynomial slots per maturity (load_poly)
     if (MODEL == SABR_DYN_I) {
       for (int j = lane; j < n_mats; j += G) {
         const PolyCoef<R> c = dynamic_coef<R, false>(xp, l2f, sq.mT[j]);
@@ -243,6 +469,8 @@ __device__ __forceinline__ typename CostOf<R>::T group_cost(const R* xp, int n_q
         coef[CS * j + 1] = c.c1;
         coef[CS * j + 2] = c.c2;
       }
+    } else if constexpr (sizeof(R) == 4) {
+      case2_group_coef_rule(xp, n_mats, l2f, sq, coef, coef + 4 * n_mats, lane, G, gmask);
     } else {
       case2_group_coef<R>(xp, n_mats, l2f, sq, coef, lane, G, gmask);
     }

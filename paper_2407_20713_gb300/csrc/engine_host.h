@@ -19,6 +19,13 @@ struct HostProblem {
   double x0[kMaxD], lo[kMaxD], hi[kMaxD];
   double T0 = 0.0, step0 = 0.0, step_min = 0.0;
   uint64_t seed = 0;
+  int chain0 = 0;  // global index of chain 0 (chain-sharded problems)
+  // FP32 Case II term-structure rule (case2_rule_build): per node (u, W,
+  // tau, 0), per sub-panel (half width, sum of W, sum of tau W, 0), per
+  // maturity (first sub-panel, sub-panel count)
+  std::vector<float> c2_node, c2_sub;
+  std::vector<int> c2_panel;
+  int c2_nsub = 0;
 };
 
 sabr_status formula_prepare(const sabr_problem& pr, const sabr_bounds& b, const sabr_cooling& c, uint64_t seed,
@@ -28,8 +35,11 @@ sabr_status formula_prepare(const sabr_problem& pr, const sabr_bounds& b, const 
 // [1, 32]) sets it for every problem; results then differ only by the FP32
 // rounding of the lane sums.
 int choose_lanes(int n_quotes, int n_mats, int model, long long batch_chains);
-// Dynamic shared memory of a level block (cpb chains) / of an init block.
-size_t level_smem_bytes(int prec, int model, int Q, int M, int cpb);
+// Dynamic shared memory of a level block (cpb chains) / of an init block;
+// c2_nsub: sub-panels of the FP32 Case II rule (0 otherwise).
+size_t level_smem_bytes(int prec, int model, int Q, int M, int cpb, int c2_nsub = 0);
+// Most sub-panels an FP32 Case II rule may have (8 nodes each).
+constexpr int kMaxC2Sub = 128;
 size_t init_smem_bytes(const HostProblem& h);
 // Lays out one problem's device region at [off0, end) of an arena: its
 // quotes, schedule, start point, chain state and block partials, filling d.

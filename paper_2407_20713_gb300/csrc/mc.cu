@@ -43,10 +43,16 @@ __host__ __device__ inline McSmem mc_smem_layout(int n_steps, int n_quotes, int 
 // sets whose set_valid flag is 0 are skipped.  Writes, per block, the FP64
 // sums of payoff and payoff^2 of every option to
 // partial[(s * blocks_per_set + block) * n_slots * 32 + value].
+// block0 / grid_total (path sharding): this launch runs blocks block0 ..
+// block0 + gridDim.x - 1 of a grid of grid_total blocks -- each block takes
+// the paths it would take in that grid -- and writes their partials at
+// positions 0 .. gridDim.x - 1; grid_total = 0 means the launch is the
+// whole grid.
 template <class R>
 __global__ void __launch_bounds__(kMcBlock) mc_paths_kernel(McDev P, const double* __restrict__ set_params,
                                                            const int* __restrict__ set_valid,
-                                                           double* __restrict__ partial) {
+                                                           double* __restrict__ partial, int block0,
+                                                           int grid_total) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int set = blockIdx.y;
   if (set_valid && !set_valid[set]) return;
@@ -76,8 +82,9 @@ __global__ void __launch_bounds__(kMcBlock) mc_paths_kernel(McDev P, const doubl
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5;
+  const int64_t gblocks = grid_total > 0 ? grid_total : gridDim.x;
   simulate_paths<R>(P, p, tab, land, s_q0, s_nq, s_slot, sK, scall,
-                    (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x,
+                    (int64_t)(block0 + blockIdx.x) * blockDim.x + threadIdx.x, gblocks * blockDim.x,
                     wacc + (size_t)warp * nv);
   __syncthreads();
   double* out = partial + ((size_t)set * gridDim.x + blockIdx.x) * nv;
@@ -232,6 +239,10 @@ void mc_fill_image(const McHost& h, unsigned char* host_img, unsigned char* dev_
   d.log_absorb = std::log(1e-12 * h.fwd);
   d.key0 = (uint32_t)h.seed;
   d.key1 = (uint32_t)(h.seed >> 32);
+  for (int r = 0; r < 10; ++r) {  // Philox round keys (key schedule of Salmon et al.)
+    d.rk.k0[r] = d.key0 + (uint32_t)r * 0x9E3779B9u;
+    d.rk.k1[r] = d.key1 + (uint32_t)r * 0xBB67AE85u;
+  }
   d.step_t = (const double*)put(h.step_t.data(), 8 * h.step_t.size());
   d.step_h = (const double*)put(h.step_h.data(), 8 * h.step_h.size());
   d.step_mat = (const int*)put(h.step_mat.data(), 4 * h.step_mat.size());
@@ -285,17 +296,21 @@ int mc_blocks_per_set(const McHost& h, int n_sets) {
   return (int)best;
 }
 
+static void launch_paths(const McHost& h, const McDev& d, const double* set_params, const int* set_valid,
+                         dim3 grid, double* partial, int block0, int grid_total, cudaStream_t s) {
+  if (h.prec == SABR_FP64) {
+    set_mc_smem<double>(h.smem);
+    mc_paths_kernel<double><<<grid, kMcBlock, h.smem, s>>>(d, set_params, set_valid, partial, block0, grid_total);
+  } else {
+    set_mc_smem<float>(h.smem);
+    mc_paths_kernel<float><<<grid, kMcBlock, h.smem, s>>>(d, set_params, set_valid, partial, block0, grid_total);
+  }
+}
+
 sabr_status mc_launch(const McHost& h, const McDev& d, const double* set_params, const int* set_valid, int n_sets,
                       int blocks_per_set, double* partial, const int* q_value, const int* q_out,
                       const double* disc, double* price, double* se, int out_stride, cudaStream_t s) {
-  dim3 grid(blocks_per_set, n_sets);
-  if (h.prec == SABR_FP64) {
-    set_mc_smem<double>(h.smem);
-    mc_paths_kernel<double><<<grid, kMcBlock, h.smem, s>>>(d, set_params, set_valid, partial);
-  } else {
-    set_mc_smem<float>(h.smem);
-    mc_paths_kernel<float><<<grid, kMcBlock, h.smem, s>>>(d, set_params, set_valid, partial);
-  }
+  launch_paths(h, d, set_params, set_valid, dim3(blocks_per_set, n_sets), partial, 0, 0, s);
   const int total = n_sets * h.n_quotes;
   mc_reduce_kernel<<<(total + 127) / 128, 128, 0, s>>>(d, n_sets, blocks_per_set, partial, q_value, q_out, disc,
                                                        set_valid, price, se, out_stride);
@@ -375,5 +390,122 @@ extern "C" sabr_status sabr_mc_price(sabr_model model, const double* params, dou
   SABR_TRY(mc_launch(h, d, (const double*)(base + params_off), nullptr, 1, bps, (double*)(base + part_off), q_value,
                      q_out, disc, price_out, stderr_out, (int)n, s));
   SABR_CUDA(cudaEventRecord(w.done, s));
+  return SABR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Path sharding (the multi-GPU form of the Sec. 4 pricer): the grid of
+// sabr_mc_price split into block ranges, one per device; the per-block FP64
+// partial sums, gathered in block order, reduce to the unsharded prices bit
+// for bit.
+// ---------------------------------------------------------------------------
+namespace sabr {
+
+struct McShardCall {
+  McHost h;
+  int total_blocks = 0;
+};
+
+static sabr_status mc_shard_prepare(sabr_model model, const double* params, double fwd, const double* T,
+                                    const double* K, const int8_t* is_call, const double* discount, int64_t n,
+                                    int64_t n_paths, double spy, uint64_t seed, sabr_precision prec, McShardCall& c) {
+  SABR_TRY(check_params(model, params));
+  SABR_TRY(mc_prepare(model, fwd, T, K, is_call, discount, n, n_paths, spy, seed, prec, c.h));
+  if (model == SABR_DYN_II && !case2_feasible<double, double>(params, c.h.Tmax))
+    return fail(SABR_EINVAL, "parameters violate rho(t) in [-1,1], nu(t) > 0");
+  c.total_blocks = mc_blocks_per_set(c.h, 1);
+  return SABR_OK;
+}
+
+// Uploads the tables and parameters into the per-device workspace; returns
+// the device image and the workspace (whose `done` event the caller records).
+static sabr_status mc_shard_upload(const McShardCall& c, const double* params, cudaStream_t s, McDev& d,
+                                   int** q_value, int** q_out, double** disc, const double** dparams,
+                                   McWorkspace** ws) {
+  const size_t img = mc_image_bytes(c.h);
+  const size_t params_off = (img + 255) & ~(size_t)255;
+  const size_t part_off = params_off + 256;
+  int dev = 0;
+  SABR_CUDA(cudaGetDevice(&dev));
+  if ((int)g_mc_ws.size() <= dev) g_mc_ws.resize(dev + 1);
+  McWorkspace& w = g_mc_ws[dev];
+  SABR_TRY(ensure_ws(w, part_off, part_off));
+  unsigned char* base = (unsigned char*)w.dev;
+  mc_fill_image(c.h, w.host, base, d, q_value, q_out, disc);
+  double p10[kMaxD];
+  for (int i = 0; i < kMaxD; ++i) p10[i] = i < n_params(c.h.model) ? params[i] : 0.0;
+  std::memcpy(w.host + params_off, p10, sizeof(p10));
+  SABR_CUDA(cudaMemcpyAsync(w.dev, w.host, part_off, cudaMemcpyHostToDevice, s));
+  *dparams = (const double*)(base + params_off);
+  *ws = &w;
+  return SABR_OK;
+}
+
+}  // namespace sabr
+
+extern "C" sabr_status sabr_mc_shard_layout(sabr_model model, const double* params, double fwd, const double* T,
+                                            const double* K, const int8_t* is_call, const double* discount,
+                                            int64_t n, int64_t n_paths, double steps_per_year, uint64_t seed,
+                                            sabr_precision prec, int32_t* total_blocks,
+                                            int64_t* doubles_per_block) {
+  using namespace sabr;
+  clear_error();
+  if (!total_blocks || !doubles_per_block) return fail(SABR_EINVAL, "NULL output");
+  McShardCall c;
+  SABR_TRY(mc_shard_prepare(model, params, fwd, T, K, is_call, discount, n, n_paths, steps_per_year, seed, prec, c));
+  *total_blocks = c.total_blocks;
+  *doubles_per_block = (int64_t)c.h.n_slots * 32;
+  return SABR_OK;
+}
+
+extern "C" sabr_status sabr_mc_shard_partials(sabr_model model, const double* params, double fwd, const double* T,
+                                              const double* K, const int8_t* is_call, const double* discount,
+                                              int64_t n, int64_t n_paths, double steps_per_year, uint64_t seed,
+                                              sabr_precision prec, int32_t total_blocks, int32_t block_begin,
+                                              int32_t block_count, double* partials_out, void* stream) {
+  using namespace sabr;
+  clear_error();
+  if (!partials_out) return fail(SABR_EINVAL, "partials_out is NULL");
+  std::lock_guard<std::mutex> lock(g_mc_mutex);
+  McShardCall c;
+  SABR_TRY(mc_shard_prepare(model, params, fwd, T, K, is_call, discount, n, n_paths, steps_per_year, seed, prec, c));
+  if (total_blocks < 1 || block_count < 1 || block_begin < 0 || (int64_t)block_begin + block_count > total_blocks)
+    return fail(SABR_EINVAL, "block range outside [0, total_blocks)");
+  cudaStream_t s = (cudaStream_t)stream;
+  McDev d;
+  int *q_value, *q_out;
+  double* disc;
+  const double* dp;
+  McWorkspace* w;
+  SABR_TRY(mc_shard_upload(c, params, s, d, &q_value, &q_out, &disc, &dp, &w));
+  launch_paths(c.h, d, dp, nullptr, dim3(block_count, 1), partials_out, block_begin, total_blocks, s);
+  SABR_CUDA(cudaGetLastError());
+  SABR_CUDA(cudaEventRecord(w->done, s));
+  return SABR_OK;
+}
+
+extern "C" sabr_status sabr_mc_shard_reduce(sabr_model model, const double* params, double fwd, const double* T,
+                                            const double* K, const int8_t* is_call, const double* discount,
+                                            int64_t n, int64_t n_paths, double steps_per_year, uint64_t seed,
+                                            sabr_precision prec, int32_t total_blocks, const double* partials,
+                                            double* price_out, double* stderr_out, void* stream) {
+  using namespace sabr;
+  clear_error();
+  if (!partials || !price_out) return fail(SABR_EINVAL, "NULL partials or price_out");
+  std::lock_guard<std::mutex> lock(g_mc_mutex);
+  McShardCall c;
+  SABR_TRY(mc_shard_prepare(model, params, fwd, T, K, is_call, discount, n, n_paths, steps_per_year, seed, prec, c));
+  if (total_blocks < 1) return fail(SABR_EINVAL, "total_blocks must be >= 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  McDev d;
+  int *q_value, *q_out;
+  double* disc;
+  const double* dp;
+  McWorkspace* w;
+  SABR_TRY(mc_shard_upload(c, params, s, d, &q_value, &q_out, &disc, &dp, &w));
+  mc_reduce_kernel<<<(c.h.n_quotes + 127) / 128, 128, 0, s>>>(d, 1, total_blocks, partials, q_value, q_out, disc,
+                                                               nullptr, price_out, stderr_out, (int)n);
+  SABR_CUDA(cudaGetLastError());
+  SABR_CUDA(cudaEventRecord(w->done, s));
   return SABR_OK;
 }

@@ -20,6 +20,8 @@ struct McDev {
   int64_t n_paths;
   double fwd, log_absorb;  // ln(1e-12 f)
   uint32_t key0, key1;
+  PhiloxKeys rk;           // the ten round keys of (key0, key1): kernel
+                           // parameters, read as constants by the path loop
   const double* step_t;    // [n_steps] right end t_{i+1} of step i, where
                            // its nu(t), rho(t) are taken
   const double* step_h;    // [n_steps] length of step i
@@ -137,7 +139,7 @@ template <class R> struct PathState {
 };
 
 __device__ __forceinline__ uint4 path_words(const McDev& P, int64_t path, int i) {
-  return philox4x32_10(make_uint4((uint32_t)path, (uint32_t)(i >> 1), 0u, kTagMC), P.key0, P.key1);
+  return philox4x32_10(make_uint4((uint32_t)path, (uint32_t)(i >> 1), 0u, kTagMC), P.rk);
 }
 
 template <class R>

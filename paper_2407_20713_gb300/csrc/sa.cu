@@ -40,23 +40,51 @@ template <class R>
 __device__ __forceinline__ SmemQuotes<R> stage_quotes(const ProblemDev& P, unsigned char* base,
                                                       int nthreads, int tid, unsigned char** end) {
   const int Q = P.n_quotes, M = P.n_mats;
+  // Q + 1 quote slots: the pair layout of an odd count needs one more
   QuotePack<R>* pack = (QuotePack<R>*)base;  // base is 16-byte aligned
-  R* l2k = (R*)(pack + Q);
+  R* l2k = (R*)(pack + Q + 1);
   R* mT = l2k + Q;
   const bool dyn = P.model == SABR_DYN_I || P.model == SABR_DYN_II;
-  for (int i = tid; i < Q; i += nthreads) {
-    QuotePack<R> qp;
-    qp.lfk = ((const R*)P.q_lfk)[i];
-    qp.l2kf = dyn ? mat_in_slot(P.q_mat[i], R{}) : ((const R*)P.q_l2kf)[i];
-    qp.T = ((const R*)P.q_T)[i];
-    qp.w = ((const R*)P.q_w)[i];
-    pack[i] = qp;
-    l2k[i] = ((const R*)P.q_l2k)[i];
+  if (sizeof(R) == 4 && P.model == SABR_HAGAN) {
+    float4* pr = (float4*)base;
+    const float* lfk = (const float*)P.q_lfk;
+    const float* l2kf = (const float*)P.q_l2kf;
+    const float* T = (const float*)P.q_T;
+    const float* w = (const float*)P.q_w;
+    for (int j = tid; j < (Q + 1) / 2; j += nthreads) {
+      const int i0 = 2 * j, i1 = 2 * j + 1;
+      const bool two = i1 < Q;
+      pr[2 * j] = make_float4(lfk[i0], two ? lfk[i1] : 0.0f, l2kf[i0], two ? l2kf[i1] : 0.0f);
+      pr[2 * j + 1] = make_float4(T[i0], two ? T[i1] : 0.0f, -w[i0], two ? -w[i1] : 0.0f);
+    }
+  } else {
+    for (int i = tid; i < Q; i += nthreads) {
+      QuotePack<R> qp;
+      qp.lfk = ((const R*)P.q_lfk)[i];
+      qp.l2kf = dyn ? mat_in_slot(P.q_mat[i], R{}) : ((const R*)P.q_l2kf)[i];
+      qp.T = ((const R*)P.q_T)[i];
+      qp.w = ((const R*)P.q_w)[i];
+      pack[i] = qp;
+      l2k[i] = ((const R*)P.q_l2k)[i];
+    }
   }
   for (int j = tid; j < M; j += nthreads) mT[j] = ((const R*)P.m_T)[j];
-  unsigned char* e = (unsigned char*)(mT + M);
-  *end = (unsigned char*)(((uintptr_t)e + 15) & ~(uintptr_t)15);
-  SmemQuotes<R> sq{pack, l2k, mT};
+  unsigned char* e = (unsigned char*)(((uintptr_t)(mT + M) + 15) & ~(uintptr_t)15);
+  SmemQuotes<R> sq{pack, (const float4*)base, l2k, mT, nullptr, nullptr, nullptr};
+  if (sizeof(R) == 4 && P.model == SABR_DYN_II) {
+    // the Case II term-structure rule: nodes, sub-panels, maturity panels
+    float4* nd = (float4*)e;
+    float4* sb = nd + kC2Nodes * P.c2_nsub;
+    int2* pn = (int2*)(sb + P.c2_nsub);
+    for (int i = tid; i < kC2Nodes * P.c2_nsub; i += nthreads) nd[i] = P.c2_node[i];
+    for (int i = tid; i < P.c2_nsub; i += nthreads) sb[i] = P.c2_sub[i];
+    for (int i = tid; i < M; i += nthreads) pn[i] = P.c2_panel[i];
+    sq.c2_node = nd;
+    sq.c2_sub = sb;
+    sq.c2_panel = pn;
+    e = (unsigned char*)(((uintptr_t)(pn + M) + 15) & ~(uintptr_t)15);
+  }
+  *end = e;
   return sq;
 }
 
@@ -76,6 +104,12 @@ __device__ __forceinline__ void warp_argmin(double& f, int& i) {
     argmin_merge(f, i, f2, i2);
   }
 }
+
+// Quote pairs per point the speculative Hagan loop keeps in flight (two
+// points are evaluated at once, so fewer than QueuePairs).
+template <class R> struct SpecPairs {
+  static constexpr int value = 2;
+};
 
 template <int MODEL> struct Dim {
   static constexpr int value = MODEL == SABR_DYN_II ? 10 : (MODEL == SABR_DYN_I ? 6 : 4);
@@ -196,7 +230,7 @@ __global__ void sa_init_kernel(const ProblemDev* __restrict__ probs, const int* 
 // counters, block minima) is read from L2 (ld.global.cg), never from a
 // possibly stale L1 line.  `q` (plans only) receives the units of the next
 // level when this block closes level `level` of problem `pid`.
-template <class R, int MODEL>
+template <class R, int MODEL, int PAIRS = 2>
 __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int pid, int blk, int level, unsigned char* smem,
                                                const LevelQueue* q) {
   unsigned char* rest;
@@ -206,7 +240,7 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int pid, int
   const int g = threadIdx.x / G, lane = threadIdx.x % G;
   // per-maturity polynomial slices exist only for the dynamic models
   const int coef_m = (MODEL == SABR_DYN_I || MODEL == SABR_DYN_II) ? P.n_mats : 0;
-  constexpr int CS = CoefStride<MODEL>::value;
+  constexpr int CS = CoefStride<R, MODEL>::value;
   R* coef = (R*)rest + (size_t)g * CS * coef_m;
   double* red_f = (double*)((R*)rest + (size_t)cpb * CS * coef_m + 16);
   red_f = (double*)(((uintptr_t)red_f + 15) & ~(uintptr_t)15);
@@ -215,30 +249,37 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int pid, int
 
   const int chain = blk * cpb + g;
   const bool active = chain < P.n_chains;
+  const uint32_t gchain = (uint32_t)(P.chain0 + chain);  // Philox counter word 0
   const unsigned gmask = group_mask(G);
 
-  const double T0 = __ldcg(&P.state[kMaxD + 1]);
-  const double Tk = __dmul_rn(T0, P.ck[level]);
-  double sk = __dmul_rn(P.step0, __dsqrt_rn(__ddiv_rn(Tk, T0)));
-  if (sk < P.step_min) sk = P.step_min;
-
-  // box and step widths of this level, shared by the block's chains (kept
-  // in shared memory rather than registers)
+  // temperature, step widths and box of this level, formed once by thread 0
+  // (FP64 division and square root issue at a small fraction of the FP32
+  // rate) and shared by the block's chains
   __shared__ R s_lo[kMaxD], s_hi[kMaxD], s_step[kMaxD];
-  if (threadIdx.x < D) {
-    const int i = threadIdx.x;
-    s_step[i] = (R)__dmul_rn(sk, __dsub_rn(P.hi[i], P.lo[i]));
-    s_lo[i] = (R)P.lo[i];
-    s_hi[i] = (R)P.hi[i];
+  __shared__ double s_Tk;
+  __shared__ float s_invTk;
+  if (threadIdx.x == 0) {
+    const double T0 = __ldcg(&P.state[kMaxD + 1]);
+    const double Tk0 = __dmul_rn(T0, P.ck[level]);
+    double sk = __dmul_rn(P.step0, __dsqrt_rn(__ddiv_rn(Tk0, T0)));
+    if (sk < P.step_min) sk = P.step_min;
+    for (int i = 0; i < D; ++i) {
+      s_step[i] = (R)__dmul_rn(sk, __dsub_rn(P.hi[i], P.lo[i]));
+      s_lo[i] = (R)P.lo[i];
+      s_hi[i] = (R)P.hi[i];
+    }
+    s_Tk = Tk0;
+    s_invTk = (float)(1.4426950408889634 / Tk0);  // log2(e) / T_k: FP32 Metropolis in base 2
   }
   __syncthreads();
+  const double Tk = s_Tk;
   R x[D];
 #pragma unroll
   for (int i = 0; i < D; ++i) x[i] = (R)__ldcg(&P.state[i]);
   using C = typename CostOf<R>::T;
   C fcur = cost_from(__ldcg(&P.state[kMaxD]), C{});
   C bf = fcur;
-  const float inv_Tk = (float)(1.4426950408889634 / Tk);  // log2(e) / T_k: FP32 Metropolis in base 2
+  const float inv_Tk = s_invTk;
   // the chain's best point lives in its chain_bx row (written by lane 0 on
   // each improvement), not in registers
   R* cbx = (R*)P.chain_bx + (size_t)chain * kMaxD;
@@ -257,14 +298,124 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int pid, int
   const R Tmax = (R)P.Tmax;
 
   if (active) {
+    // The FP32 static formulas draw one Philox block per proposal on one lane
+    // and keep the ten round keys in registers; the other forms (whose
+    // lanes share the draws, or whose register budget is tight) step the
+    // key schedule in every block.
+    constexpr bool kRoundKeys = sizeof(R) == 4 && (MODEL == SABR_HAGAN || MODEL == SABR_OBLOJ);
+    PhiloxKeys pk;
+    if constexpr (kRoundKeys) pk = philox_keys(P.key0, P.key1);
+    const uint32_t key0 = P.key0, key1 = P.key1;
+    auto draw = [&](uint4 c) {
+      if constexpr (kRoundKeys) {
+        return philox4x32_10(c, pk);
+      } else {
+        return philox4x32_10(c, key0, key1);
+      }
+    };
+    bool ran_spec = false;
+    if constexpr (MODEL == SABR_HAGAN) {
+      if (P.spec) {
+        // Speculative acceptance (Hagan).  Acceptance is the common outcome
+        // (with T0 = f(x0) about 95% of the proposals on the benchmark
+        // surfaces), so each iteration forms step st's proposal xa from x
+        // and step st+1's proposal xb from xa, as if xa were accepted, and
+        // evaluates both (group_cost2_hagan: per point the arithmetic and
+        // order of group_cost).  If step st accepts, step st+1 is decided
+        // with xb's cost and the chain advances two steps; otherwise xb is
+        // dropped and step st+1 is drawn again from x.  The trajectory,
+        // counters and best point are those of the one-step loop below.
+        ran_spec = true;
+        auto words = [&](int s) { return draw(make_uint4(gchain, (uint32_t)level, (uint32_t)s, kTagSA)); };
+        uint4 w0 = words(0), w1 = words(1);
+        int st = 0;
+        while (st < P.chain_len) {
+          const uint4 w2 = words(st + 2), w3 = words(st + 3);  // off the critical path
+          R ua[D + 1], ub[D + 1];
+          ua[0] = u01<R>(w0.x);
+          ua[1] = u01<R>(w0.y);
+          ua[2] = u01<R>(w0.z);
+          ua[3] = u01<R>(w0.w);
+          ua[D] = u01<R>(sa_accept_word(w0.x, w0.y, w0.z));
+          ub[0] = u01<R>(w1.x);
+          ub[1] = u01<R>(w1.y);
+          ub[2] = u01<R>(w1.z);
+          ub[3] = u01<R>(w1.w);
+          ub[D] = u01<R>(sa_accept_word(w1.x, w1.y, w1.z));
+          R xa[D], xb[D];
+          bool in_a = true, in_b = true;
+#pragma unroll
+          for (int i = 0; i < D; ++i) {
+            xa[i] = propose(x[i], s_step[i], ua[i]);
+            in_a = in_a && !(xa[i] < s_lo[i] || xa[i] > s_hi[i]);
+            xb[i] = propose(xa[i], s_step[i], ub[i]);
+            in_b = in_b && !(xb[i] < s_lo[i] || xb[i] > s_hi[i]);
+          }
+          int adv = 1;
+          if (in_a) {
+            C fa, fb;
+            group_cost2_hagan<R, SpecPairs<R>::value>(xa, xb, P.n_quotes, sq, lane, G, gmask, fa, fb);
+            ++ev;
+            bool acc_a = false;
+            if (!cost_is_nan(fa)) {
+              if (cost_less(fa, bf)) {
+                bf = fa;
+                if (lane == 0) {
+#pragma unroll
+                  for (int i = 0; i < D; ++i) cbx[i] = xa[i];
+                }
+              }
+              const auto da = cost_delta(fa, fcur);
+              acc_a = da <= 0 || metropolis(ua[D], da, inv_Tk, Tk);
+            }
+            if (acc_a) {
+#pragma unroll
+              for (int i = 0; i < D; ++i) x[i] = xa[i];
+              fcur = fa;
+              ++ac;
+              if (st + 1 < P.chain_len) {
+                adv = 2;
+                if (in_b) {
+                  ++ev;
+                  if (!cost_is_nan(fb)) {
+                    if (cost_less(fb, bf)) {
+                      bf = fb;
+                      if (lane == 0) {
+#pragma unroll
+                        for (int i = 0; i < D; ++i) cbx[i] = xb[i];
+                      }
+                    }
+                    const auto db = cost_delta(fb, fcur);
+                    if (db <= 0 || metropolis(ub[D], db, inv_Tk, Tk)) {
+#pragma unroll
+                      for (int i = 0; i < D; ++i) x[i] = xb[i];
+                      fcur = fb;
+                      ++ac;
+                    }
+                  }
+                }
+              }
+            }
+          }
+          if (adv == 1) {
+            w0 = w1;
+            w1 = w2;
+          } else {
+            w0 = w2;
+            w1 = w3;
+          }
+          st += adv;
+        }
+      }
+    }
     uint4 wbuf = make_uint4(0u, 0u, 0u, 0u);
     constexpr int NB = sa_philox_blocks(D);  // Philox blocks per step
     const int S = G >= NB ? G / NB : 1;  // steps per batch of Philox blocks
     int s_ctr = 0;                         // st mod S
     uint4 wnext = make_uint4(0u, 0u, 0u, 0u);
-    if (NB == 1 && G == 1)
-      wnext = philox4x32_10(make_uint4((uint32_t)chain, (uint32_t)level, 0u, kTagSA), P.key0, P.key1);
-    for (int st = 0; st < P.chain_len; ++st) {
+    if (NB == 1 && G == 1 && !ran_spec)
+      wnext = draw(make_uint4(gchain, (uint32_t)level, 0u, kTagSA));
+    for (int st = 0; st < (ran_spec ? 0 : P.chain_len); ++st) {
       // D Philox words of blocks 0, 1, ... with counter (chain, level, step,
       // tag + block): D move uniforms and, from their unused low bits, the
       // acceptance uniform (sa_accept_word).  With G >= NB lanes, the chain's
@@ -278,8 +429,7 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int pid, int
         // formed here, off the critical path of this one (its counter does
         // not depend on this step's outcome)
         const uint4 w = wnext;
-        wnext = philox4x32_10(make_uint4((uint32_t)chain, (uint32_t)level, (uint32_t)(st + 1), kTagSA), P.key0,
-                              P.key1);
+        wnext = draw(make_uint4(gchain, (uint32_t)level, (uint32_t)(st + 1), kTagSA));
         wv[0] = w.x;
         wv[1] = w.y;
         wv[2] = w.z;
@@ -289,9 +439,7 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int pid, int
         s_ctr = s_ctr + 1 == S ? 0 : s_ctr + 1;
         if (s_in == 0) {
           const int l = lane < S * NB ? lane : 0;
-          wbuf = philox4x32_10(make_uint4((uint32_t)chain, (uint32_t)level, (uint32_t)(st + l / NB),
-                                          kTagSA + (uint32_t)(l % NB)),
-                               P.key0, P.key1);
+          wbuf = draw(make_uint4(gchain, (uint32_t)level, (uint32_t)(st + l / NB), kTagSA + (uint32_t)(l % NB)));
         }
         const int base = ((threadIdx.x & 31) & ~(G - 1)) + s_in * NB;
 #pragma unroll
@@ -303,9 +451,7 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int pid, int
       } else {
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-          const uint4 w = philox4x32_10(
-              make_uint4((uint32_t)chain, (uint32_t)level, (uint32_t)st, kTagSA + (uint32_t)b), P.key0,
-              P.key1);
+          const uint4 w = draw(make_uint4(gchain, (uint32_t)level, (uint32_t)st, kTagSA + (uint32_t)b));
           wv[4 * b + 0] = w.x;
           wv[4 * b + 1] = w.y;
           wv[4 * b + 2] = w.z;
@@ -325,7 +471,7 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int pid, int
       }
       if (MODEL == SABR_DYN_II && inside) inside = case2_feasible<R>(xp, Tmax);
       if (!inside) continue;
-      const C fp = group_cost<R, MODEL>(xp, P.n_quotes, P.n_mats, l2f, sq, coef, lane, G, gmask);
+      const C fp = group_cost<R, MODEL, PAIRS>(xp, P.n_quotes, P.n_mats, l2f, sq, coef, lane, G, gmask);
       ++ev;
       if (cost_is_nan(fp)) continue;
       if (cost_less(fp, bf)) {
@@ -397,6 +543,7 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int pid, int
       for (int w = 1; w < (int)(blockDim.x >> 5); ++w) argmin_merge(f, bb, s_wf[w], s_wb[w]);
       for (int i = 0; i < kMaxD; ++i) P.state[i] = __ldcg(&P.part_x[(size_t)bb * kMaxD + i]);
       P.state[kMaxD] = f;
+      P.state[kStateArgChain] = (double)(P.chain0 + __ldcg(&P.part_c[bb]));
       *P.arrive = 0u;
     }
     if (q != nullptr && level + 1 < P.n_levels) {
@@ -422,10 +569,12 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int pid, int
 // level in .z (level < 0), so that one captured launch serves every step
 // whatever its mix of requests.  Both use this one kernel, so a problem's
 // arithmetic is the same machine code in a plan and in the server.
-// Register budget: the static formulas' quote loop runs three quotes at a
-// time (up to 128 registers); the polynomial and dynamic models keep 80.
+// Register budget: up to 128 registers for the static formulas' quote loop
+// (pairs of quotes), the dynamic term structures (Case I closed forms, the
+// Case II rule's eight node values and thirteen running sums per panel) and
+// the chain state; the expanded form keeps 80.
 template <class R, int MODEL> struct LevelMinBlocks {
-  static constexpr int value = sizeof(R) == 8 ? 1 : (MODEL == SABR_HAGAN || MODEL == SABR_OBLOJ ? 2 : 3);
+  static constexpr int value = sizeof(R) == 8 ? 1 : (MODEL == SABR_EXPANDED ? 3 : 2);
 };
 
 template <class R, int MODEL>
@@ -446,8 +595,21 @@ __global__ void __launch_bounds__(kSaBlock, (LevelMinBlocks<R, MODEL>::value))
 
 // Every level of a plan's launch group in one launch: each block takes units
 // from the ready queue until all are claimed (or a wait gave up).
+// Resident 64-thread blocks per SM the queue kernel is compiled for: the
+// FP32 static formulas run four (two warps a scheduler, up to 255 registers
+// for the quote-pair loop), the FP32 dynamic models eight (128 registers;
+// their term structures are latency-bound and want more warps), the
+// expanded form twelve at 80 registers, the FP64 form four.
+template <class R, int MODEL> struct QueueBlocks {
+  static constexpr int value =
+      sizeof(R) == 8 ? 4 : ((MODEL == SABR_HAGAN || MODEL == SABR_OBLOJ) ? 4 : (MODEL == SABR_EXPANDED ? 12 : 8));
+};
+template <class R, int MODEL> struct QueuePairs {
+  static constexpr int value = 5;
+};
+
 template <class R, int MODEL>
-__global__ void __launch_bounds__(kLevelBlock, (4 * LevelMinBlocks<R, MODEL>::value))
+__global__ void __launch_bounds__(kLevelBlock, (QueueBlocks<R, MODEL>::value))
     sa_queue_kernel(const ProblemDev* __restrict__ probs, LevelQueue q) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ ProblemDev P;
@@ -468,7 +630,7 @@ __global__ void __launch_bounds__(kLevelBlock, (4 * LevelMinBlocks<R, MODEL>::va
     const int lv = (int)((e >> 23) & (kQueueMaxLevels - 1));
     const int blk = (int)(e & (kQueueMaxBlocks - 1));
     load_problem(probs, pid, &P);
-    sa_level_block<R, MODEL>(P, pid, blk, lv, smem, &q);
+    sa_level_block<R, MODEL, QueuePairs<R, MODEL>::value>(P, pid, blk, lv, smem, &q);
     __syncthreads();
   }
 }
@@ -539,9 +701,11 @@ __global__ void __launch_bounds__(kSaBlock) sa_finalize_kernel(const ProblemDev*
     if (P.n_levels == 0 || c == 0x7fffffff) {
       f = P.state[kMaxD];
       for (int i = 0; i < kMaxD; ++i) s_best[i] = P.state[i];
+      P.state[kStateBestChain] = -1.0;
     } else {
       const R* bx = (const R*)P.chain_bx + (size_t)c * kMaxD;
       for (int i = 0; i < kMaxD; ++i) s_best[i] = (double)bx[i];
+      P.state[kStateBestChain] = (double)(P.chain0 + c);
     }
     sabr_result* r = P.result;
     for (int i = 0; i < kMaxD; ++i) {
@@ -602,6 +766,14 @@ __global__ void __launch_bounds__(kSaBlock) sa_finalize_kernel(const ProblemDev*
 // ---------------------------------------------------------------------------
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Whether Hagan problems use the speculative step loop (sa_level_block):
+// the environment variable SABR_SPECULATE=0 selects the one-step loop (the
+// same results; kept for comparison).
+static bool speculate_enabled() {
+  const char* e = std::getenv("SABR_SPECULATE");
+  return !(e && e[0] == '0');
+}
+
 static int next_pow2(int v) {
   int p = 1;
   while (p < v) p <<= 1;
@@ -634,18 +806,69 @@ int choose_lanes(int n_quotes, int n_mats, int model, long long batch_chains) {
   return G;
 }
 
-size_t level_smem_bytes(int prec, int model, int Q, int M, int cpb) {
+size_t level_smem_bytes(int prec, int model, int Q, int M, int cpb, int c2_nsub) {
   const size_t rs = prec == SABR_FP64 ? 8 : 4;
   const size_t cm = (model == SABR_DYN_I || model == SABR_DYN_II) ? (size_t)M : 0;
-  size_t b = 4 * rs * (size_t)Q + ((size_t)Q + M) * rs;  // pack, l2k, mT
+  size_t b = 4 * rs * ((size_t)Q + 1) + ((size_t)Q + M) * rs;  // pack (or pairs), l2k, mT
   b = align_up(b, 16);
-  b += (size_t)cpb * coef_stride(model) * cm * rs + 16 * rs;
+  if (prec == SABR_FP32 && model == SABR_DYN_II)  // Case II rule: nodes, sub-panels, panels
+    b = align_up(b + (size_t)c2_nsub * (kC2Nodes + 1) * 16 + (size_t)M * 8, 16);
+  b += (size_t)cpb * coef_stride(prec, model) * cm * rs + 16 * rs;
   b = align_up(b, 16) + 16;
   b += (size_t)cpb * 8 + (size_t)cpb * kMaxD * rs;
   return align_up(b, 16) + 64;
 }
 
-size_t init_smem_bytes(const HostProblem& h) { return level_smem_bytes(h.prec, SABR_DYN_II, h.n_quotes, h.n_mats, 1); }
+size_t init_smem_bytes(const HostProblem& h) {
+  return level_smem_bytes(h.prec, SABR_DYN_II, h.n_quotes, h.n_mats, 1, h.c2_nsub);
+}
+
+// The FP32 Case II term-structure rule of a problem: the maturities split
+// [0, Tmax] into panels [T_{j-1}, T_j], and each panel into sub-panels no
+// wider than max(start, 2/k) (k the largest exponential rate the box allows:
+// 2b for nu^2, a + b for nu rho); an 8-point Gauss-Legendre rule on each
+// sub-panel.  The widths grow geometrically away from t = 0, so e^{-k' t}
+// is resolved for every rate k' <= k: where a sub-panel is wide (k' h
+// large) the exponential is already negligible at its start.
+static sabr_status case2_rule_build(HostProblem& h) {
+  h.c2_node.clear();
+  h.c2_sub.clear();
+  h.c2_panel.clear();
+  const double amax = std::max(std::fabs(h.lo[4]), std::fabs(h.hi[4]));
+  const double bmax = std::max(std::fabs(h.lo[5]), std::fabs(h.hi[5]));
+  const double kmax = std::max(2.0 * bmax, amax + bmax);
+  const double w0 = kmax > 0.0 ? 2.0 / kmax : 1e300;
+  constexpr GaussRule<kC2Nodes> gr = make_gauss<kC2Nodes>();
+  double prev = 0.0;
+  int nsub = 0;
+  for (int j = 0; j < h.n_mats; ++j) {
+    const double T = h.mT[j];
+    h.c2_panel.push_back(nsub);
+    int cnt = 0;
+    double s0 = prev;
+    for (;;) {
+      double e = s0 + std::max(s0, w0);
+      if (e >= T || T - e < 0.5 * std::max(e, w0)) e = T;
+      const double hh = 0.5 * (e - s0);
+      double sw = 0.0, stw = 0.0;
+      for (int k = 0; k < kC2Nodes; ++k) {
+        const double u = s0 + hh * (1.0 + gr.x[k]), W = hh * gr.w[k];
+        h.c2_node.insert(h.c2_node.end(), {(float)u, (float)W, (float)(T - u), 0.0f});
+        sw += W;
+        stw += (T - u) * W;
+      }
+      h.c2_sub.insert(h.c2_sub.end(), {(float)hh, (float)sw, (float)stw, 0.0f});
+      ++cnt;
+      if (++nsub > kMaxC2Sub) return fail(SABR_EINVAL, "Case II rate bounds too wide for the FP32 term-structure rule");
+      if (e >= T) break;
+      s0 = e;
+    }
+    h.c2_panel.push_back(cnt);
+    prev = T;
+  }
+  h.c2_nsub = nsub;
+  return SABR_OK;
+}
 
 sabr_status formula_prepare(const sabr_problem& pr, const sabr_bounds& b, const sabr_cooling& c, uint64_t seed,
                             HostProblem& h) {
@@ -711,6 +934,7 @@ sabr_status formula_prepare(const sabr_problem& pr, const sabr_bounds& b, const 
   }
   if (h.model == SABR_DYN_II && !case2_feasible<double, double>(h.x0, h.Tmax))
     return fail(SABR_EINVAL, "x0 violates the Case II constraints");
+  if (h.model == SABR_DYN_II && h.prec == SABR_FP32) SABR_TRY(case2_rule_build(h));
   h.ck.resize(std::max(h.n_levels, 1));
   for (int k = 0; k < h.n_levels; ++k) h.ck[k] = std::pow(c.factor, (double)k);
   return SABR_OK;
@@ -763,6 +987,8 @@ size_t formula_layout(const HostProblem& h, int G, unsigned char* img, unsigned 
   const size_t o_ck = take(h.ck.size() * 8), o_x0 = take(kMaxD * 8), o_state = take(kStateLen * 8);
   const size_t o_bf = take(C * 8), o_bx = take(C * kMaxD * rs), o_ev = take(C * 8), o_ac = take(C * 8);
   const size_t o_pf = take(B * 8), o_pc = take(B * 4), o_px = take(B * kMaxD * 8), o_arr = take(4);
+  const size_t o_c2n = take(4 * h.c2_node.size()), o_c2s = take(4 * h.c2_sub.size()),
+               o_c2p = take(4 * h.c2_panel.size());
   if (write) {
     if (h.prec == SABR_FP64) {
       put(o_lfk, h.lfk.data(), Q * 8);
@@ -797,6 +1023,9 @@ size_t formula_layout(const HostProblem& h, int G, unsigned char* img, unsigned 
     put(o_ck, h.ck.data(), h.ck.size() * 8);
     put(o_x0, h.x0, kMaxD * 8);
     std::memset(img + o_arr, 0, 4);
+    put(o_c2n, h.c2_node.data(), 4 * h.c2_node.size());
+    put(o_c2s, h.c2_sub.data(), 4 * h.c2_sub.size());
+    put(o_c2p, h.c2_panel.data(), 4 * h.c2_panel.size());
   }
   d.q_lfk = base + o_lfk;
   d.q_l2kf = base + o_l2kf;
@@ -823,6 +1052,12 @@ size_t formula_layout(const HostProblem& h, int G, unsigned char* img, unsigned 
   d.part_x = (double*)(base + o_px);
   d.arrive = (unsigned int*)(base + o_arr);
   d.result = dres;
+  d.c2_node = (const float4*)(base + o_c2n);
+  d.c2_sub = (const float4*)(base + o_c2s);
+  d.c2_panel = (const int2*)(base + o_c2p);
+  d.c2_nsub = h.c2_nsub;
+  d.chain0 = h.chain0;
+  d.spec = (h.model == SABR_HAGAN && speculate_enabled()) ? 1 : 0;
   return o;
 }
 
@@ -920,12 +1155,14 @@ struct LaunchGroup {
 // aims for: four give every SM scheduler two warps, so all schedulers carry
 // the same load (the environment variable SABR_WORKERS_PER_SM overrides it
 // for tuning).
-static int workers_per_sm() {
+static int workers_per_sm(int prec, int model) {
   if (const char* e = std::getenv("SABR_WORKERS_PER_SM")) {
     const int w = std::atoi(e);
     if (w >= 1 && w <= 32) return w;
   }
-  return 4;
+  int w = 4;
+  SABR_DISPATCH(prec, model, (w = QueueBlocks<R, M>::value));
+  return w;
 }
 // Whether plans may use the ready queue: the environment variable
 // SABR_PLAN_QUEUE=0 makes them launch their levels one by one instead (the
@@ -1065,8 +1302,8 @@ static sabr_status build_plan(int32_t n, const sabr_problem* problems, const sab
   std::vector<size_t> f_off(nf), mc_off(p->mc.size());
   for (int i = 0; i < nf; ++i) {
     lanes[i] = choose_lanes(hp[i].n_quotes, hp[i].n_mats, hp[i].model, batch_chains);
-    if (level_smem_bytes(hp[i].prec, hp[i].model, hp[i].n_quotes, hp[i].n_mats, kLevelBlock / lanes[i]) >
-        kMaxLevelSmem) {
+    if (level_smem_bytes(hp[i].prec, hp[i].model, hp[i].n_quotes, hp[i].n_mats, kLevelBlock / lanes[i],
+                         hp[i].c2_nsub) > kMaxLevelSmem) {
       free_plan(p);
       return fail(SABR_EINVAL, "the quotes of a problem exceed one block's shared memory at its precision");
     }
@@ -1088,7 +1325,7 @@ static sabr_status build_plan(int32_t n, const sabr_problem* problems, const sab
     g->total_blocks += pd[i].n_blocks;
     g->max_levels = std::max(g->max_levels, hp[i].n_levels);
     g->smem_level = std::max(g->smem_level, level_smem_bytes(hp[i].prec, hp[i].model, hp[i].n_quotes, hp[i].n_mats,
-                                                              pd[i].cpb));
+                                                              pd[i].cpb, hp[i].c2_nsub));
     g->smem_init = std::max(g->smem_init, init_smem_bytes(hp[i]));
     p->max_levels = std::max(p->max_levels, hp[i].n_levels);
   }
@@ -1109,8 +1346,14 @@ static sabr_status build_plan(int32_t n, const sabr_problem* problems, const sab
       const double per_step = (double)(hp[pi].n_quotes / lanes[pi] + 1) + 64.0 * hp[pi].n_mats + 64.0;
       unit_ns = std::max(unit_ns, 100.0 * per_step * (double)hp[pi].chain_len);
     }
-    g.use_queue = queue_enabled() && nf <= kQueueMaxProblems && p->max_levels < kQueueMaxLevels &&
-                  total * 8 <= kMaxQueueBytes;
+    // The queue pays when a level of the group has more units than the
+    // persistent grid has blocks and several problems can fill each
+    // other's level ends; a single problem (every unit of a level waits for
+    // the same restart point) runs level by level.
+    const int per_sm = std::min(workers_per_sm(g.prec, g.model), queue_blocks_per_sm(g.prec, g.model, g.smem_level));
+    const int grid = std::max(1, std::min(g.total_blocks, sms * per_sm));
+    g.use_queue = queue_enabled() && g.problems.size() > 1 && g.total_blocks > grid && nf <= kQueueMaxProblems &&
+                  p->max_levels < kQueueMaxLevels && total * 8 <= kMaxQueueBytes;
     for (int pi : g.problems) g.use_queue = g.use_queue && pd[pi].n_blocks <= kQueueMaxBlocks;
     if (g.use_queue) {
       g.q.total = total;
@@ -1119,8 +1362,7 @@ static sabr_status build_plan(int32_t n, const sabr_problem* problems, const sab
       qent_off[gi] = take(8 * std::max<unsigned long long>(total, 1));
       qctl_off[gi] = take(32);
       ql0_off[gi] = take(8 * std::max<size_t>(level0[gi].size(), 1));
-      const int per_sm = std::min(workers_per_sm(), queue_blocks_per_sm(g.prec, g.model, g.smem_level));
-      g.queue_grid = std::max(1, std::min(g.total_blocks, sms * per_sm));
+      g.queue_grid = grid;
     }
   }
   const size_t arena_bytes = align_up(o, 256);

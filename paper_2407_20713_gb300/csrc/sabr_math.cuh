@@ -145,6 +145,49 @@ template <int N> __host__ __device__ constexpr GaussRule<N> make_gauss() {
 // Device copies of the rules, constant-initialised at compile time.
 template <int N> __constant__ GaussRule<N> kGaussRule = make_gauss<N>();
 
+// Integration matrix of the N-point Gauss-Legendre rule: S[k][i] is the
+// integral over [-1, x_k] of the i-th Lagrange basis polynomial of the nodes,
+// so that sum_i S[k][i] f(x_i) integrates the interpolant of f from -1 to
+// node k.  Each basis polynomial has degree N - 1, so the N-point rule
+// mapped to [-1, x_k] integrates it exactly.
+template <int N> struct GaussIntMatrix {
+  double S[N][N];
+};
+template <int N> __host__ __device__ constexpr GaussIntMatrix<N> make_gauss_int() {
+  GaussIntMatrix<N> m{};
+  const GaussRule<N> g = make_gauss<N>();
+  for (int k = 0; k < N; ++k)
+    for (int i = 0; i < N; ++i) {
+      double acc = 0.0;
+      for (int q = 0; q < N; ++q) {
+        const double y = -1.0 + (g.x[q] + 1.0) * (g.x[k] + 1.0) * 0.5;
+        double l = 1.0;
+        for (int r = 0; r < N; ++r)
+          if (r != i) l *= (y - g.x[r]) / (g.x[i] - g.x[r]);
+        acc += g.w[q] * (g.x[k] + 1.0) * 0.5 * l;
+      }
+      m.S[k][i] = acc;
+    }
+  return m;
+}
+// FP32 copies for the Case II term-structure rule (8 nodes a sub-panel).
+constexpr int kC2Nodes = 8;
+struct C2Tables {
+  float S[kC2Nodes][kC2Nodes];  // integration matrix
+  float w[kC2Nodes];            // weights on [-1, 1]
+};
+__host__ __device__ constexpr C2Tables make_c2_tables() {
+  C2Tables t{};
+  const GaussIntMatrix<kC2Nodes> m = make_gauss_int<kC2Nodes>();
+  const GaussRule<kC2Nodes> g = make_gauss<kC2Nodes>();
+  for (int k = 0; k < kC2Nodes; ++k) {
+    t.w[k] = (float)g.w[k];
+    for (int i = 0; i < kC2Nodes; ++i) t.S[k][i] = (float)m.S[k][i];
+  }
+  return t;
+}
+__constant__ C2Tables kC2 = make_c2_tables();
+
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64
 // multiplications, key bumped by the golden-ratio Weyl constants.
@@ -160,6 +203,34 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     c = make_uint4(hb ^ c.y ^ k0, lb, ha ^ c.w ^ k1, la);
     k0 += 0x9E3779B9u;
     k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+// The same generator with its ten round keys formed once (they depend on
+// the key only): a caller drawing many blocks under one key keeps them in
+// registers instead of stepping the key schedule in every block.
+struct PhiloxKeys {
+  uint32_t k0[10], k1[10];
+};
+__device__ __forceinline__ PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {
+  PhiloxKeys pk;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    pk.k0[r] = k0;
+    pk.k1[r] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return pk;
+}
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKeys& pk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t ma = 0xD2511F53u, mb = 0xCD9E8D57u;
+    const uint64_t pa = (uint64_t)ma * c.x, pb = (uint64_t)mb * c.z;
+    const uint32_t ha = (uint32_t)(pa >> 32), la = (uint32_t)pa;
+    const uint32_t hb = (uint32_t)(pb >> 32), lb = (uint32_t)pb;
+    c = make_uint4(hb ^ c.y ^ pk.k0[r], lb, ha ^ c.w ^ pk.k1[r], la);
   }
   return c;
 }
@@ -352,6 +423,54 @@ __device__ __forceinline__ R vol_hagan(const StaticConst<R>& s, R lfk, R l2kf, R
 // eq. (sigma-SABR): z = nu (f^{1-b} - K^{1-b}) / (alpha (1-b)); the
 // difference is K^{1-b} expm1((1-b) ln(f/K)), its b -> 1 limit ln(f/K);
 // nu ln(f/K)/x(z) = (alpha ln(f/K)/zd) (z/x(z)), alpha/K^{1-b} at K = f.
+// ---------------------------------------------------------------------------
+// Two quotes of eq. (haganf) at once, FP32.  GB300's packed FP32 forms
+// (FFMA2 / FMUL2 / FADD2, __ffma2_rn and friends) do two lanes' worth of
+// FP32 arithmetic in one issue slot, so the formula's ~30 adds and
+// multiplies per quote take half the issue slots of the scalar form; the
+// SFU operations and the branch selects stay per element.  Same operations,
+// in the same order and contraction, as vol_hagan<float> with
+// z_over_x_parts<float>; returns the residuals r = 1 + v * (-1/market) of
+// both quotes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+__device__ __forceinline__ float2 hagan_resid_pair(const StaticConst<float>& s, float2 lfk, float2 l2kf, float2 T,
+                                                   float2 wneg) {
+  const float2 e = mul2(f2(s.half_omb), l2kf);
+  const float2 fk = make_float2(ex2_approx(e.x), ex2_approx(e.y));
+  const float2 L2 = mul2(lfk, lfk);
+  const float2 den = fma2(L2, fma2(f2(s.c4), L2, f2(s.c2)), f2(1.0f));
+  const float2 z = mul2(mul2(f2(s.nu_over_alpha), lfk), fk);
+  // z / x(z): near branch (|t| < 0.2) by the atanh series, far branch by
+  // the logarithm, both formed and one selected per element
+  const float2 zr = add2(z, f2(-s.zx.rho));
+  const float2 y = fma2(zr, zr, f2(s.zx.q0));
+  const float2 D = mul2(y, make_float2(rsqrt_approx(y.x), rsqrt_approx(y.y)));
+  const float2 onepD = add2(D, f2(1.0f));
+  const float2 t = mul2(z, make_float2(rcp_approx(onepD.x), rcp_approx(onepD.y)));
+  const float2 t2 = mul2(t, t);
+  float2 S2 = fma2(f2(2.0f / 9.0f), t2, f2(2.0f / 7.0f));
+  S2 = fma2(S2, t2, f2(2.0f / 5.0f));
+  S2 = fma2(S2, t2, f2(2.0f / 3.0f));
+  S2 = fma2(S2, t2, f2(2.0f));
+  const float2 lg = make_float2(lg2_approx(D.x + fabsf(zr.x)), lg2_approx(D.y + fabsf(zr.y)));
+  const float2 cs = make_float2(zr.x > 0.0f ? -s.zx.ln_omr : -s.zx.ln_opr, zr.y > 0.0f ? -s.zx.ln_omr : -s.zx.ln_opr);
+  const float2 ax = fma2(lg, f2(0.69314718055994531f), cs);
+  const bool nx = fabsf(t.x) < 0.2f, ny = fabsf(t.y) < 0.2f;
+  const float2 zn = make_float2(fabsf(nx ? onepD.x : z.x), fabsf(ny ? onepD.y : z.y));
+  const float2 xd = make_float2(fabsf(nx ? S2.x : ax.x), fabsf(ny ? S2.y : ax.y));
+  // sigma = (z/x) [fk^2 (alpha + alpha br_c T) + (alpha br_b fk + alpha br_a) T] / (fk^3 den)
+  const float2 fk2 = mul2(fk, fk);
+  const float2 num = fma2(fk2, fma2(f2(s.abr_c), T, f2(s.alpha)), mul2(fma2(f2(s.abr_b), fk, f2(s.abr_a)), T));
+  const float2 dd = mul2(mul2(mul2(fk2, fk), den), xd);
+  const float2 v = mul2(mul2(zn, num), make_float2(rcp_approx(dd.x), rcp_approx(dd.y)));
+  return fma2(v, wneg, f2(1.0f));
+}
+
 template <class R>
 __device__ __forceinline__ R vol_obloj(const StaticConst<R>& s, R lfk, R l2kf, R l2k, R T) {
   const R kpow = m_exp2(s.omb * l2k);  // K^{1-beta}

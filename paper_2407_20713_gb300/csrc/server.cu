@@ -144,7 +144,9 @@ static size_t server_smem(int prec, int model, int max_quotes) {
   // only for M <= 2)
   const size_t rs = prec == SABR_FP64 ? 8 : 4;
   size_t b = level_smem_bytes(prec, SABR_HAGAN, max_quotes, kMaxMats, 256);
-  if (model == SABR_DYN_I || model == SABR_DYN_II) b += 512 * coef_stride(model) * rs + 64;
+  if (model == SABR_DYN_I || model == SABR_DYN_II) b += 512 * coef_stride(prec, model) * rs + 64;
+  // the FP32 Case II term-structure rule at its largest
+  if (model == SABR_DYN_II && prec == SABR_FP32) b += (size_t)kMaxC2Sub * (kC2Nodes + 1) * 16 + kMaxMats * 8 + 16;
   return b;
 }
 
@@ -486,7 +488,8 @@ static sabr_status submit(sabr_server* s, const sabr_problem* pr, const sabr_bou
     r->bytes = formula_layout(r->hp, r->G, nullptr, nullptr, 0, tmp, nullptr) + 256;
     r->n_blocks = tmp.n_blocks;
     if (r->n_blocks > kWorkPerGroup) return fail(SABR_EINVAL, "request has too many chains for one step");
-    const size_t need = level_smem_bytes(r->hp.prec, r->hp.model, r->hp.n_quotes, r->hp.n_mats, tmp.cpb);
+    const size_t need =
+        level_smem_bytes(r->hp.prec, r->hp.model, r->hp.n_quotes, r->hp.n_mats, tmp.cpb, r->hp.c2_nsub);
     if (need > s->smem[group_of(r->hp.prec, r->hp.model)])
       return fail(SABR_EINVAL, "request needs more shared memory than the server reserves");
   }

@@ -24,7 +24,8 @@ def lib():
 
 def test_header_declares_the_hot_path_entry_points():
     names = declared_functions()
-    for required in ("sabr_implied_vol", "sabr_mc_price", "sabr_calibrate"):
+    for required in ("sabr_implied_vol", "sabr_mc_price", "sabr_calibrate", "sabr_shard_level",
+                     "sabr_mc_shard_partials"):
         assert required in names
 
 
@@ -43,7 +44,8 @@ def test_struct_layouts_match_the_header(lib, tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     structs = {"sabr_problem": capi.Problem, "sabr_bounds": capi.Bounds, "sabr_cooling": capi.Cooling,
-               "sabr_result": capi.Result}
+               "sabr_result": capi.Result, "sabr_chain_point": capi.ChainPoint,
+               "sabr_server_config": capi.ServerConfig, "sabr_server_stats": capi.ServerStats}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "sabr.h"', "int main(void){"]
     expect = []
     for cname, py in structs.items():
@@ -59,6 +61,12 @@ def test_struct_layouts_match_the_header(lib, tmp_path):
     subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     assert got == expect
+
+
+def test_binding_declares_every_exported_entry_point():
+    from paper_2407_20713_gb300 import capi
+    missing = [n for n in declared_functions() if n not in capi.SIGNATURES]
+    assert not missing, missing
 
 
 def test_binding_refuses_to_run_without_the_library(tmp_path, monkeypatch):

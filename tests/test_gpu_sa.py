@@ -140,8 +140,9 @@ def test_graph_replay_equals_direct_launches_and_repeats():
     for x, y, z in zip(direct, r1, r2):
         assert np.array_equal(x.params, y.params) and np.array_equal(y.params, z.params)
         assert x.misfit == y.misfit == z.misfit and x.n_evals == y.n_evals == z.n_evals
-    # init, queue reset, one persistent launch for all levels, finalize
-    assert n_launch == 1 + 2 + 1 and ms > 0
+    # a level of this plan has fewer units than the GPU has resident blocks,
+    # so it runs level by level: init, 10 levels, finalize
+    assert n_launch == 1 + 10 + 1 and ms > 0
 
 
 def test_ready_queue_equals_level_by_level_launches(monkeypatch):
@@ -158,7 +159,15 @@ def test_ready_queue_equals_level_by_level_launches(monkeypatch):
                                  n_chains=90, n_levels=7, chain_len=10, seed=33),
            sg.CalibrationProblem(model=sg.HAGAN, T=T15, K=K15, market=mkt, lo=LO4, hi=HI4, prec=sg.FP32,
                                  n_chains=64, n_levels=0, chain_len=20, seed=34)]
-    queued = sg.calibrate_batch(pbs)
+    plan = sg.Plan(pbs, use_graph=True)
+    plan.run()
+    queued = plan.results()
+    n_launch, _ = plan.stats()
+    plan.close()
+    # FP32 Hagan group (three problems, more units per level than resident
+    # blocks): init, queue reset, one persistent launch, finalize; the FP64
+    # Case I group (one problem): init, 7 levels, finalize
+    assert n_launch == 2 + 2 + 7 + 2
     monkeypatch.setenv("SABR_PLAN_QUEUE", "0")
     plan = sg.Plan(pbs, use_graph=True)
     plan.run()
@@ -358,3 +367,78 @@ def test_fp32_and_fp64_outcomes_have_the_same_distribution_over_seeds():
         med32, med64 = np.median(out[sg.FP32]), np.median(out[sg.FP64])
         assert 0.7 <= med32 / med64 <= 1.43, (i, med32, med64)
         assert out[sg.FP32].min() <= 1.1 * out[sg.FP64].min(), (i, out[sg.FP32].min(), out[sg.FP64].min())
+
+
+CASE2_TRUTH = [0.25, 0.8, -0.4, 0.6, 0.8, 0.9, 0.1, 0.15, 0.2, -0.1]
+CASE2_LO = [0.05, 0.5, -1.0, 0.01, 0.0, 0.0, -0.5, -0.5, -1.0, -1.0]
+
+
+@pytest.mark.parametrize("model,truth,lo,hi,mats", [
+    (sg.HAGAN, TRUTH, LO4, HI4, [0.1, 1.0, 5.0]),
+    (sg.OBLOJ, TRUTH, LO4, HI4, [0.1, 1.0, 5.0]),
+    (sg.EXPANDED, TRUTH, LO4, HI4, [0.1, 1.0, 5.0]),
+    (sg.DYN_I, [0.25, 0.8, -0.5, 0.7, 0.6, 0.9], [0.05, 0.5, -1.0, 0.01, 0.0, 0.0], [0.6, 1.0, 1.0, 1.5, 5.0, 5.0],
+     [0.1, 0.25, 0.5, 1.0, 2.0, 5.0, 10.0]),
+    # Case II: the composite term-structure rule of the FP32 form, with the
+    # cfg-3 box (rates up to 5), a box up to the paper's b = 150 (Sec. 6.2),
+    # one long maturity, and 30 years
+    (sg.DYN_II, CASE2_TRUTH, CASE2_LO,
+     [0.6, 1.0, 1.0, 1.5, 5.0, 5.0, 0.5, 0.5, 1.0, 1.0], [0.1, 0.25, 0.5, 0.75, 1, 1.5, 2, 3, 4, 5, 7, 10]),
+    (sg.DYN_II, [0.25, 0.8, -0.4, 0.6, 40.0, 120.0, 0.1, 0.15, 0.2, 0.3], CASE2_LO,
+     [0.6, 1.0, 1.0, 1.5, 150.0, 150.0, 0.5, 0.5, 1.0, 1.0], [0.05, 0.5, 1.0, 5.0]),
+    (sg.DYN_II, CASE2_TRUTH, CASE2_LO, [0.6, 1.0, 1.0, 1.5, 5.0, 5.0, 0.5, 0.5, 1.0, 1.0], [10.0]),
+    (sg.DYN_II, [0.25, 0.8, -0.4, 0.6, 0.05, 0.1, 0.1, 0.15, 0.02, -0.01], CASE2_LO,
+     [0.6, 1.0, 1.0, 1.5, 5.0, 5.0, 0.5, 0.5, 1.0, 1.0], [0.5, 2.0, 10.0, 30.0]),
+])
+def test_fp32_in_loop_cost_matches_the_oracle(model, truth, lo, hi, mats):
+    # With no levels the returned misfit is the FP32 in-loop cost of x0
+    # (init kernel, the same group_cost as every proposal).  On a noise-free
+    # surface at the true point it is the sum of the squared FP32 relative
+    # vol errors (eq. error_calibrate_relativo with market = oracle vols);
+    # at a perturbed point it must equal the oracle's misfit.
+    K1 = np.linspace(0.5, 1.6, 21)
+    T = np.repeat(np.asarray(mats, dtype=float), K1.size)
+    K = np.tile(K1, len(mats))
+    ref = O.implied_vol(model, truth, 1.0, T, K)
+    ok = ref > 0.02
+    T, K, ref = T[ok], K[ok], ref[ok]
+    base = dict(model=model, T=T, K=K, market=ref, lo=lo, hi=hi, prec=sg.FP32, n_chains=8, n_levels=0)
+    g = sg.calibrate(sg.CalibrationProblem(x0=truth, **base))
+    assert g.status == 0
+    rms = np.sqrt(g.misfit / T.size)
+    print("in-loop FP32 rms relative vol error", model, mats, rms)
+    assert rms <= 3e-6, (model, rms)
+    x1 = np.array(truth, dtype=float)
+    x1[0] *= 1.03
+    x1[2] = x1[2] + 0.05
+    g1 = sg.calibrate(sg.CalibrationProblem(x0=x1, **base))
+    # the FP32 form holds its points in FP32: the oracle evaluates the point
+    # as returned (x1 rounded to FP32)
+    o1 = O.misfit(O.implied_vol(model, g1.params, 1.0, T, K), ref)
+    assert np.allclose(g1.params, x1[:len(g1.params)], rtol=1e-7)
+    assert g1.misfit == pytest.approx(o1, rel=2e-4), (model, g1.misfit, o1)
+    assert g1.misfit_fp64 == pytest.approx(o1, rel=1e-9)
+
+
+@pytest.mark.parametrize("prec", [sg.FP32, sg.FP64])
+def test_speculative_hagan_loop_equals_the_one_step_loop(prec, monkeypatch):
+    # Hagan chains evaluate step st and, as if it were accepted, step st+1
+    # together; the results (best point, restart point, misfits, counters)
+    # must be those of the one-step loop bit for bit, with one lane per
+    # chain (a large batch: the persistent launch) and with many (one small
+    # problem: lanes share its quotes)
+    mkt = market()
+    T, K = np.repeat([0.5, 2.0], 15), np.tile(K15, 2)
+    m2 = market(T=T, K=K, seed=4)
+    pbs = [sg.CalibrationProblem(model=sg.HAGAN, T=T, K=K, market=m2, lo=LO4, hi=HI4, prec=prec,
+                                 n_chains=4000, n_levels=6, chain_len=31, seed=41 + i) for i in range(3)]
+    small = sg.CalibrationProblem(model=sg.HAGAN, T=T15, K=K15, market=mkt, lo=LO4, hi=HI4, prec=prec,
+                                  n_chains=48, n_levels=8, chain_len=40, seed=44)
+    spec = sg.calibrate_batch(pbs) + [sg.calibrate(small)]
+    monkeypatch.setenv("SABR_SPECULATE", "0")
+    plain = sg.calibrate_batch(pbs) + [sg.calibrate(small)]
+    for a, b in zip(spec, plain):
+        assert a.status == b.status == 0
+        assert np.array_equal(a.params, b.params) and np.array_equal(a.restart_params, b.restart_params)
+        assert a.misfit == b.misfit and a.misfit_fp64 == b.misfit_fp64
+        assert a.n_evals == b.n_evals and a.n_accepts == b.n_accepts
