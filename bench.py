@@ -43,6 +43,18 @@ HAGAN_QUOTE_OPS = {"ex2": 1, "rsq": 1, "lg2": 1, "rcp": 2, "fp32": 30}
 # nu-hat, ~12 FP32 operations, and half a Philox4x32-10 block (ten rounds of
 # two 32x32 multiplies, each a low and a high half: 20 integer multiplies).
 MC_STEP_OPS = {"lg2": 1, "rsq": 1, "sin": 2, "ex2": 1, "fp32": 12, "imad": 20}
+# Algorithmic work of one dynamic-model proposal on the 12 x 21 joint
+# surface.  Case I: per maturity the Case I functions (four short series of
+# about 20 FMAs each, or their closed forms) and the polynomial of eq.
+# (vola_SABRd) -- about 120 FP32 operations, one exp2 and a few
+# reciprocals -- and per quote 4 FP32 (polynomial and misfit term).  Case
+# II: per node of the shared rule (96 nodes) two exp2 and about 30 FP32
+# operations; per maturity a recurrence step and the polynomial (about 41
+# FP32, one exp2, five reciprocals); per quote 4 FP32.
+DYN_PROPOSAL_OPS = {
+    1: {"ex2": 12, "rcp": 60, "fp32": 12 * 120 + 252 * 4},
+    2: {"ex2": 96 * 2 + 12, "rcp": 60, "fp32": 96 * 30 + 12 * 41 + 252 * 4},
+}
 SMS = 152
 
 
@@ -456,7 +468,7 @@ def measure_mc_calibration(sg, torch, stream, rates, sm_mhz):
     return res
 
 
-def measure_dynamic(sg, torch, stream, levels=N_LEVELS):
+def measure_dynamic(sg, torch, stream, levels=N_LEVELS, rates=None, sm_mhz=None):
     """Joint dynamic fits on 12 maturities x 21 strikes, 8192 chains each, one
     Case I and one Case II surface, FP32; `levels` of the 200 levels."""
     from paper_2407_20713_gb300 import workloads
@@ -478,6 +490,12 @@ def measure_dynamic(sg, torch, stream, levels=N_LEVELS):
         ms = a.elapsed_time(b)
         res["case%d" % case] = {"value": r.n_evals / (ms / 1e3), "unit": "cost-evals/s", "ms": ms,
                                 "levels": levels, "quote_evals_per_s": r.n_evals * 252 / (ms / 1e3)}
+        if rates and sm_mhz:
+            peak, pipe, _ = pipe_bound(DYN_PROPOSAL_OPS[case], rates, sm_mhz)
+            res["case%d" % case]["roofline"] = {
+                "bound": "alu", "pipe": pipe, "unit": "cost-evals/s", "peak": peak,
+                "achieved": r.n_evals / (ms / 1e3), "frac": r.n_evals / (ms / 1e3) / peak,
+                "ops_per_proposal": DYN_PROPOSAL_OPS[case]}
         plan.close()
     return res
 
@@ -840,7 +858,7 @@ def run_ours(args):
                         ("single_smile", lambda: measure_single_smile(sg, torch, stream)),
                         ("mc_calibration", lambda: measure_mc_calibration(sg, torch, stream, rates, sm_mhz)),
                         ("cliquet", lambda: measure_cliquet(sg, torch, stream, rates, sm_mhz)),
-                        ("dynamic", lambda: measure_dynamic(sg, torch, stream)),
+                        ("dynamic", lambda: measure_dynamic(sg, torch, stream, rates=rates, sm_mhz=sm_mhz)),
                         ("serving", lambda: measure_serving_loads(sg, args.serve_requests))):
             try:
                 line[key] = fn()

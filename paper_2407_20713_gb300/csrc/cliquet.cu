@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kClqBlock) cliquet_kernel(McDev P, const doubl
     for (int i = 0; i < P.n_steps; i += 2) {
       uint4 w[NPT];
 #pragma unroll
-      for (int k = 0; k < NPT; ++k) w[k] = path_words(P, path[k], i);
+      for (int k = 0; k < NPT; ++k) w[k] = path_words<R>(P, path[k], i);
 #pragma unroll
       for (int k = 0; k < NPT; ++k) path_step<R>(tab[i], w[k].x, w[k].y, beta_m1, log_abs, st[k]);
       if (i == i_land) at_reset();

@@ -281,7 +281,7 @@ int mc_blocks_per_set(const McHost& h, int n_sets) {
   per_sm = std::min(std::max(per_sm, 1), 8);
   const int64_t resident = device_sms() * (int64_t)per_sm;
   const int64_t sets = std::max(1, n_sets);
-  const int64_t per_block = (int64_t)kMcBlock * kMcPathsPerThread;
+  const int64_t per_block = (int64_t)kMcBlock * mc_paths_per_thread(h.prec);
   const int64_t by_paths = (h.n_paths + per_block - 1) / per_block;
   const int64_t p_max = std::max<int64_t>(1, std::min(by_paths, 8 * resident / sets));
   int64_t best = 1;

@@ -4,6 +4,7 @@
 #pragma once
 #include <cstdint>
 
+#include "../../include/sabr.h"
 #include "sabr_math.cuh"
 
 namespace sabr {
@@ -138,8 +139,16 @@ template <class R> struct PathState {
   bool absorbed;
 };
 
+// The FP32 loops read the ten round keys as kernel parameters; the FP64 loop
+// (register-heavy) steps the key schedule instead.  Same words either way.
+template <class R = float>
 __device__ __forceinline__ uint4 path_words(const McDev& P, int64_t path, int i) {
-  return philox4x32_10(make_uint4((uint32_t)path, (uint32_t)(i >> 1), 0u, kTagMC), P.rk);
+  const uint4 c = make_uint4((uint32_t)path, (uint32_t)(i >> 1), 0u, kTagMC);
+  if constexpr (sizeof(R) == 4) {
+    return philox4x32_10(c, P.rk);
+  } else {
+    return philox4x32_10(c, P.key0, P.key1);
+  }
 }
 
 template <class R>
@@ -154,10 +163,16 @@ __device__ __forceinline__ void path_step(const StepCoef<R>& s, uint32_t wa, uin
   st.absorbed = st.absorbed || !(st.lnF >= log_abs);
 }
 
-// Paths per thread of the pricing kernel: independent paths advance step by
-// step together (independent dependency chains for the scheduler; three
-// measured fastest against two and four).
+// Paths per thread: independent paths advance step by step together
+// (independent dependency chains for the scheduler).  The cliquet kernel and
+// the FP64 pricer take three (measured fastest against two and four in the
+// scalar form); the FP32 pricer takes four, two pairs of paths stepped with
+// the packed FP32x2 instructions (simulate_paths<float>).
 constexpr int kMcPathsPerThread = 3;
+template <class R> struct McPathsPerThread {
+  static constexpr int value = sizeof(R) == 4 ? 4 : kMcPathsPerThread;
+};
+__host__ __device__ constexpr int mc_paths_per_thread(int prec) { return prec == SABR_FP32 ? 4 : kMcPathsPerThread; }
 
 // Simulates, with every thread of the grid, the paths path0 + k pstride
 // (k = 0 .. kMcPathsPerThread - 1), then the next kMcPathsPerThread
@@ -167,7 +182,7 @@ constexpr int kMcPathsPerThread = 3;
 // in chunks of 32 starting at slot mat_slot[m].  Steps go in pairs: one
 // Philox block per path feeds both.
 template <class R>
-__device__ __forceinline__ void simulate_paths(const McDev& P, const double* p,
+__device__ __forceinline__ void simulate_paths_scalar(const McDev& P, const double* p,
                                                const StepCoef<R>* tab, const int* land,
                                                const int* s_q0, const int* s_nq, const int* s_slot,
                                                const R* sK, const int8_t* scall, int64_t path0,
@@ -228,7 +243,7 @@ __device__ __forceinline__ void simulate_paths(const McDev& P, const double* p,
     for (int i = 0; i < n_steps; i += 2) {
       uint4 w[NPT];
 #pragma unroll
-      for (int k = 0; k < NPT; ++k) w[k] = path_words(P, path[k], i);
+      for (int k = 0; k < NPT; ++k) w[k] = path_words<R>(P, path[k], i);
       {
         const StepCoef<R> s = tab[i];
 #pragma unroll
@@ -242,6 +257,131 @@ __device__ __forceinline__ void simulate_paths(const McDev& P, const double* p,
         if (i + 1 == i_land) pay_out();
       }
     }
+  }
+}
+
+// Two FP32 paths of one log-Euler step (path_step<float>) with the packed
+// FP32x2 instructions: the adds, multiplies and FMAs of both paths share an
+// issue slot; the SFU operations and the absorption test stay per path.  The
+// normals are z1 = -r cos, z2 = -r sin; with zr1 = r cos, zr2 = r sin the
+// signs go into the step coefficients (nc = -c, nd = -d, passed negated).
+__device__ __forceinline__ void path_step2(float a, float nc, float nd, float e, uint32_t wa0, uint32_t wb0,
+                                           uint32_t wa1, uint32_t wb1, float beta_m1, float log_abs, float2& lnF,
+                                           float2& lnA, bool& abs0, bool& abs1) {
+  const float2 u1 = make_float2(u01<float>(wa0), u01<float>(wa1));
+  const float2 u2 = make_float2(u01<float>(wb0), u01<float>(wb1));
+  const float2 s2 = mul2(f2(-1.38629436111989061f), make_float2(lg2_approx(u1.x), lg2_approx(u1.y)));
+  const float2 r = mul2(s2, make_float2(rsqrt_approx(s2.x), rsqrt_approx(s2.y)));
+  const float2 ang = fma2(f2(6.28318530717958647692f), u2, f2(-3.14159265358979323846f));
+  const float2 zr1 = mul2(r, make_float2(cos_approx(ang.x), cos_approx(ang.y)));
+  const float2 zr2 = mul2(r, make_float2(sin_approx(ang.x), sin_approx(ang.y)));
+  // nu-hat from the old alpha and the old F
+  const float2 arg = fma2(f2(beta_m1), lnF, lnA);
+  const float2 nuhat = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
+  const float2 t = fma2(f2(nd), zr2, mul2(f2(nc), zr1));  // c z1 + d z2
+  lnF = fma2(nuhat, fma2(nuhat, f2(e), t), lnF);
+  const float b = a * (float)(-0.5 / PathUnits<float>::kLogUnit);
+  lnA = fma2(f2(a), fma2(zr1, f2(-1.0f), f2(b)), lnA);  // a (z1 + b)
+  abs0 = abs0 || !(lnF.x >= log_abs);
+  abs1 = abs1 || !(lnF.y >= log_abs);
+}
+
+// The FP32 path loop: four paths per thread as two pairs (path_step2); the
+// same path numbering, Philox counters, landing steps and payoff
+// accumulation as simulate_paths_scalar.
+__device__ __forceinline__ void simulate_paths_f32(const McDev& P, const double* p, const StepCoef<float>* tab,
+                                                   const int* land, const int* s_q0, const int* s_nq,
+                                                   const int* s_slot, const float* sK, const int8_t* scall,
+                                                   int64_t path0, int64_t pstride, double* wacc) {
+  constexpr int NPT = 4;
+  const int lane = threadIdx.x & 31;
+  const float beta_m1 = (float)(p[1] - 1.0);
+  const float lnf = (float)PathUnits<float>::logu(P.fwd), lna = (float)PathUnits<float>::logu(p[0]);
+  const float log_abs = (float)(P.log_absorb * PathUnits<float>::kLogUnit);
+  const int64_t n_paths = P.n_paths;
+  const int n_steps = P.n_steps;
+  const int64_t warp_path0 = path0 - lane;
+  for (int64_t wp = warp_path0; wp < n_paths; wp += NPT * pstride) {
+    int64_t path[NPT];
+    bool live[NPT], absd[NPT];
+    float2 lnF[2], lnA[2];
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+      path[k] = wp + k * pstride + lane;
+      live[k] = path[k] < n_paths;
+      absd[k] = false;
+    }
+    lnF[0] = lnF[1] = make_float2(lnf, lnf);
+    lnA[0] = lnA[1] = make_float2(lna, lna);
+    int m = 0, i_land = land[0];
+    auto pay_out = [&]() {
+      float F[NPT];
+#pragma unroll
+      for (int k = 0; k < NPT; ++k) {
+        const float lf = (k & 1) ? lnF[k >> 1].y : lnF[k >> 1].x;
+        F[k] = absd[k] || !live[k] ? 0.0f : PathUnits<float>::expu(lf);
+      }
+      const int q0 = s_q0[m], nq = s_nq[m], slot0 = s_slot[m];
+      for (int c0 = 0; c0 < 2 * nq; c0 += 32) {
+        float v[32];
+#pragma unroll
+        for (int kk = 0; kk < 32; kk += 2) {
+          const int j = (c0 + kk) >> 1;
+          float pay = 0.0f, pay2 = 0.0f;
+          if (j < nq) {
+            const float K = sK[q0 + j];
+            const bool call = scall[q0 + j] != 0;
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+              const float x = call ? (F[k] > K ? F[k] - K : 0.0f) : (K > F[k] ? K - F[k] : 0.0f);
+              const float y = live[k] ? x : 0.0f;
+              pay += y;
+              pay2 += y * y;
+            }
+          }
+          v[kk] = pay;
+          v[kk + 1] = pay2;
+        }
+        const float tot = warp_reduce_scatter32<float>(v, lane);
+        wacc[(slot0 + (c0 >> 5)) * 32 + lane] += (double)tot;
+      }
+      ++m;
+      i_land = m < P.n_mats ? land[m] : -1;
+    };
+    for (int i = 0; i < n_steps; i += 2) {
+      uint4 w[NPT];
+#pragma unroll
+      for (int k = 0; k < NPT; ++k) w[k] = path_words(P, path[k], i);
+      {
+        const StepCoef<float> s = tab[i];
+        path_step2(s.a, -s.c, -s.d, s.e, w[0].x, w[0].y, w[1].x, w[1].y, beta_m1, log_abs, lnF[0], lnA[0],
+                   absd[0], absd[1]);
+        path_step2(s.a, -s.c, -s.d, s.e, w[2].x, w[2].y, w[3].x, w[3].y, beta_m1, log_abs, lnF[1], lnA[1],
+                   absd[2], absd[3]);
+      }
+      if (i == i_land) pay_out();
+      if (i + 1 < n_steps) {
+        const StepCoef<float> s = tab[i + 1];
+        path_step2(s.a, -s.c, -s.d, s.e, w[0].z, w[0].w, w[1].z, w[1].w, beta_m1, log_abs, lnF[0], lnA[0],
+                   absd[0], absd[1]);
+        path_step2(s.a, -s.c, -s.d, s.e, w[2].z, w[2].w, w[3].z, w[3].w, beta_m1, log_abs, lnF[1], lnA[1],
+                   absd[2], absd[3]);
+        if (i + 1 == i_land) pay_out();
+      }
+    }
+  }
+}
+
+// The pricer's path loop in the working precision R.
+template <class R>
+__device__ __forceinline__ void simulate_paths(const McDev& P, const double* p, const StepCoef<R>* tab,
+                                               const int* land, const int* s_q0, const int* s_nq, const int* s_slot,
+                                               const R* sK, const int8_t* scall, int64_t path0, int64_t pstride,
+                                               double* wacc) {
+  if constexpr (sizeof(R) == 4) {
+    simulate_paths_f32(P, p, tab, land, s_q0, s_nq, s_slot, sK, scall, path0, pstride, wacc);
+  } else {
+    simulate_paths_scalar<R>(P, p, tab, land, s_q0, s_nq, s_slot, sK, scall, path0, pstride, wacc);
   }
 }
 

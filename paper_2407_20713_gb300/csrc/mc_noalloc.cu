@@ -70,7 +70,7 @@ extern "C" sabr_status sabr_mc_price_noalloc(sabr_model model, const double* par
   // a fixed grid (at most 1216 blocks), independent of the occupancy the
   // pricing kernel reaches, so the scratch bound below is a property of the
   // problem alone
-  const int64_t per_block = (int64_t)kMcBlock * kMcPathsPerThread;
+  const int64_t per_block = (int64_t)kMcBlock * mc_paths_per_thread(h.prec);
   const int bps = (int)std::min<int64_t>(1216, (h.n_paths + per_block - 1) / per_block);
   const size_t img = mc_image_bytes(h);
   const size_t params_off = (img + 255) & ~(size_t)255;

@@ -316,9 +316,10 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int pid, int
     bool ran_spec = false;
     if constexpr (MODEL == SABR_HAGAN) {
       if (P.spec) {
-        // Speculative acceptance (Hagan).  Acceptance is the common outcome
-        // (with T0 = f(x0) about 95% of the proposals on the benchmark
-        // surfaces), so each iteration forms step st's proposal xa from x
+        // Speculative acceptance (Hagan, several lanes per chain).
+        // Acceptance is the common outcome (with T0 = f(x0) about 95% of
+        // the proposals on the benchmark surfaces), so each iteration forms
+        // step st's proposal xa from x
         // and step st+1's proposal xb from xa, as if xa were accepted, and
         // evaluates both (group_cost2_hagan: per point the arithmetic and
         // order of group_cost).  If step st accepts, step st+1 is decided
@@ -595,14 +596,16 @@ __global__ void __launch_bounds__(kSaBlock, (LevelMinBlocks<R, MODEL>::value))
 
 // Every level of a plan's launch group in one launch: each block takes units
 // from the ready queue until all are claimed (or a wait gave up).
-// Resident 64-thread blocks per SM the queue kernel is compiled for: the
-// FP32 static formulas run four (two warps a scheduler, up to 255 registers
-// for the quote-pair loop), the FP32 dynamic models eight (128 registers;
-// their term structures are latency-bound and want more warps), the
-// expanded form twelve at 80 registers, the FP64 form four.
+// Resident warps per SM the queue kernel is compiled for (in blocks of
+// kLevelBlock threads): the FP32 static formulas eight (two warps a
+// scheduler, up to 255 registers for the quote-pair loop), the FP32
+// dynamic models sixteen (128 registers; their term structures are
+// latency-bound and want more warps), the expanded form 24 at 80
+// registers, the FP64 form eight.
 template <class R, int MODEL> struct QueueBlocks {
-  static constexpr int value =
-      sizeof(R) == 8 ? 4 : ((MODEL == SABR_HAGAN || MODEL == SABR_OBLOJ) ? 4 : (MODEL == SABR_EXPANDED ? 12 : 8));
+  static constexpr int warps =
+      sizeof(R) == 8 ? 8 : ((MODEL == SABR_HAGAN || MODEL == SABR_OBLOJ) ? 8 : (MODEL == SABR_EXPANDED ? 24 : 16));
+  static constexpr int value = warps * 32 / kLevelBlock;
 };
 template <class R, int MODEL> struct QueuePairs {
   static constexpr int value = 5;
@@ -766,9 +769,10 @@ __global__ void __launch_bounds__(kSaBlock) sa_finalize_kernel(const ProblemDev*
 // ---------------------------------------------------------------------------
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Whether Hagan problems use the speculative step loop (sa_level_block):
-// the environment variable SABR_SPECULATE=0 selects the one-step loop (the
-// same results; kept for comparison).
+// Whether Hagan problems whose chains have several lanes use the
+// speculative step loop (sa_level_block): the environment variable
+// SABR_SPECULATE=0 selects the one-step loop (the same results; kept for
+// comparison).
 static bool speculate_enabled() {
   const char* e = std::getenv("SABR_SPECULATE");
   return !(e && e[0] == '0');
@@ -1057,7 +1061,11 @@ size_t formula_layout(const HostProblem& h, int G, unsigned char* img, unsigned 
   d.c2_panel = (const int2*)(base + o_c2p);
   d.c2_nsub = h.c2_nsub;
   d.chain0 = h.chain0;
-  d.spec = (h.model == SABR_HAGAN && speculate_enabled()) ? 1 : 0;
+  // speculation pays where a chain's lanes share its quotes (small,
+  // latency-bound problems); with one lane per chain (large batches) the two
+  // evaluations cost more issue slots than the latency they hide (measured
+  // on the benchmark surface: 2.28e10 against 2.53e10 cost-evals/s)
+  d.spec = (h.model == SABR_HAGAN && G > 1 && speculate_enabled()) ? 1 : 0;
   return o;
 }
 

@@ -422,11 +422,11 @@ def test_fp32_in_loop_cost_matches_the_oracle(model, truth, lo, hi, mats):
 
 @pytest.mark.parametrize("prec", [sg.FP32, sg.FP64])
 def test_speculative_hagan_loop_equals_the_one_step_loop(prec, monkeypatch):
-    # Hagan chains evaluate step st and, as if it were accepted, step st+1
-    # together; the results (best point, restart point, misfits, counters)
-    # must be those of the one-step loop bit for bit, with one lane per
-    # chain (a large batch: the persistent launch) and with many (one small
-    # problem: lanes share its quotes)
+    # Hagan chains with several lanes evaluate step st and, as if it were
+    # accepted, step st+1 together; the results (best point, restart point,
+    # misfits, counters) must be those of the one-step loop bit for bit,
+    # for small problems whose lanes share the quotes (the large batch, one
+    # lane per chain, runs the one-step loop either way)
     mkt = market()
     T, K = np.repeat([0.5, 2.0], 15), np.tile(K15, 2)
     m2 = market(T=T, K=K, seed=4)
