@@ -20,6 +20,7 @@ from . import build_oracle
 
 HAGAN, OBLOJ, EXPANDED, DYN_I, DYN_II = 0, 1, 2, 3, 4
 COST_VOL, COST_MC = 0, 1
+MC_LOG_EULER, MC_BESSEL = 0, 1
 TAG_SA = 0x53410000
 TAG_MC = 0x4D430000
 
@@ -79,6 +80,11 @@ def lib():
         L.orc_mc_price.argtypes = [ctypes.c_int, _PD, _D, _PD, _PD, _PI8, _PD, _I64,
                                    _I64, _D, ctypes.c_uint64, ctypes.c_int, _PD, _PD]
         L.orc_mc_price.restype = ctypes.c_int
+        L.orc_mc_price_scheme.argtypes = [ctypes.c_int, ctypes.c_int, _PD, _D, _PD, _PD, _PI8, _PD, _I64,
+                                          _I64, _D, ctypes.c_uint64, ctypes.c_int, _PD, _PD]
+        L.orc_mc_price_scheme.restype = ctypes.c_int
+        L.orc_mb_gamma_draws.argtypes = [_D, ctypes.c_uint64, _I64, _PD]
+        L.orc_mb_gamma_draws.restype = None
         L.orc_mc_cliquet.argtypes = [ctypes.c_int, _PD, _D, _D, ctypes.c_int, _D, _D, _D, _D, _D, _I64, _D,
                                      ctypes.c_uint64, ctypes.c_int, _PD, _PD]
         L.orc_mc_cliquet.restype = ctypes.c_int
@@ -218,8 +224,9 @@ def mc_grid(T, steps_per_year):
 
 
 def mc_price(model, p, f, T, K, is_call=None, disc=None, n_paths=1 << 12,
-             steps_per_year=250.0, seed=0, n_threads=1):
-    """Sec. 4 log-Euler Monte Carlo prices and standard errors."""
+             steps_per_year=250.0, seed=0, n_threads=1, scheme=MC_LOG_EULER):
+    """Sec. 4 Monte Carlo prices and standard errors: the log-Euler scheme
+    (MC_LOG_EULER) or the conditional-Bessel step (MC_BESSEL)."""
     q = _params(p)
     T = np.ascontiguousarray(T, dtype=np.float64).ravel()
     K = np.ascontiguousarray(K, dtype=np.float64).ravel()
@@ -227,7 +234,7 @@ def mc_price(model, p, f, T, K, is_call=None, disc=None, n_paths=1 << 12,
     dc = None if disc is None else np.ascontiguousarray(disc, dtype=np.float64).ravel()
     price = np.empty(T.size)
     se = np.empty(T.size)
-    rc = lib().orc_mc_price(model, _dp(q), float(f), _dp(T), _dp(K),
+    rc = lib().orc_mc_price_scheme(int(scheme), model, _dp(q), float(f), _dp(T), _dp(K),
                             ic.ctypes.data_as(_PI8) if ic is not None else None,
                             _dp(dc), T.size, int(n_paths), float(steps_per_year),
                             int(seed) & 0xFFFFFFFFFFFFFFFF, int(n_threads),
@@ -235,6 +242,13 @@ def mc_price(model, p, f, T, K, is_call=None, disc=None, n_paths=1 << 12,
     if rc != 0:
         raise ValueError("orc_mc_price rejected its input")
     return price, se
+
+
+def mb_gamma_draws(a, n, seed=0):
+    """n Gamma(a) draws of the conditional-Bessel step's sampler."""
+    out = np.empty(int(n))
+    lib().orc_mb_gamma_draws(float(a), int(seed) & 0xFFFFFFFFFFFFFFFF, int(n), _dp(out))
+    return out
 
 
 def sa_calibrate(model, f, T, K, mkt, lo, hi, *, cost=COST_VOL, n_chains=64,

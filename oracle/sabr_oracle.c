@@ -537,10 +537,221 @@ static void mc_path(int model, const double* p, double f, const double* grid,
   }
 }
 
+/* ------------------------------------------------------------------------ */
+/* The conditional-Bessel step (the low-bias fallback Sec. 4 names)          */
+/* ------------------------------------------------------------------------ */
+/* Write the SDE as dF = alpha F^beta (rho dW + sqrt(1-rho^2) dB),
+ * dalpha = nu alpha dW, with W and B independent.  Over one step [t, t+h]
+ * (nu, rho those of the step):
+ *  1. alpha is a geometric Brownian motion: alpha' = alpha e^{x},
+ *     x = nu sqrt(h) Z_a - nu^2 h / 2 (exact).
+ *  2. The part of the forward's noise driven by W integrates exactly:
+ *     rho int alpha dW = (rho/nu)(alpha' - alpha).  For beta < 1 put
+ *     Y = F^{1-beta}/(1-beta); by Ito dY = rho alpha dW + sqrt(1-rho^2) alpha dB
+ *     - beta alpha^2 / (2 (1-beta) Y) dt.  The W part is applied at the start
+ *     of the step (Y0 = Y + (rho/nu)(alpha' - alpha), the one approximation
+ *     besides step 3), and with the clock tau = (1-rho^2) int alpha^2 ds the
+ *     rest is dY = dB_tau + (delta - 1)/(2 Y) dtau, a Bessel process of
+ *     dimension delta = 1 - beta / ((1-beta)(1-rho^2)) < 2, absorbed at 0
+ *     (Chen, Oosterlee and van der Weide reduce the forward the same way).
+ *  3. int alpha^2 ds over the step by the trapezoidal rule,
+ *     (h/2)(alpha^2 + alpha'^2).
+ *  4. Y'^2 given Y0^2 is a squared Bessel process of dimension delta absorbed
+ *     at 0, run for time tau.  Its transition is sampled exactly: with
+ *     a = 1 - delta/2 and m = Y0^2 / (2 tau), draw G ~ Gamma(a); the path is
+ *     absorbed if G >= m, else Y'^2 = tau ((N1 + sqrt(2 (m - G)))^2 + N2^2).
+ *     (Expanding the Bessel function of the absorbed transition density
+ *     gives weights e^{-m} m^{n+a} / Gamma(n+a+1) times the density of
+ *     2 tau Gamma(n+1); these are the law of a Gamma(a) variable G below m
+ *     followed by a Poisson(m - G) count n, and a Poisson(lambda/2) mixture
+ *     of chi-square laws with 2 + 2n degrees is the noncentral chi-square
+ *     with 2 degrees and noncentrality lambda = 2 (m - G): the square of a
+ *     normal of mean sqrt(lambda) plus the square of a standard normal.  The
+ *     total weight, the probability of not being absorbed, is
+ *     P(G < m) = P(a, m), the regularised lower incomplete gamma function.)
+ *     With rho^2 = 1 the clock stops and the drift integrates alone:
+ *     Y'^2 = Y0^2 - beta/(1-beta) int alpha^2 ds (absorbed if <= 0).
+ *  5. beta = 1: Y = ln F, Y' = Y + (rho/nu)(alpha' - alpha) - V/2
+ *     + sqrt((1-rho^2) V) N1 with V the integral of step 3; no absorption.
+ * The shift (rho/nu)(alpha' - alpha) is formed as alpha rho sqrt(h) expm1(x)
+ * / (nu sqrt(h)), which is alpha rho sqrt(h) Z_a at nu = 0.
+ * With nu = 0 and rho = 0 every step is exact: the scheme then samples the
+ * absorbed CEV law itself, at any step size.
+ *
+ * Random numbers of step i (grid index) of path j, Philox blocks with
+ * counter (j, i, b, ORC_TAG_MB):
+ *   block 0: (Z_a, N1) = BoxMuller(u(w0), u(w1)), (N2, X_0) = BoxMuller(u(w2), u(w3))
+ *   block 1: U_0 = u(w0), U_b = u(w1)
+ *   block k + 1 (k = 1 .. 7, drawn only when needed): X_k = first output of
+ *            BoxMuller(u(w0), u(w1)), U_k = u(w2)
+ * Gamma(a) by Marsaglia and Tsang's method (ACM TOMS 26(3), 2000): with
+ * a' = a (a >= 1) or a + 1 (a < 1), d = a' - 1/3, c = 1/sqrt(9 d), trial k
+ * forms v = (1 + c X_k)^3 and accepts d v when v > 0 and either
+ * U_k < 1 - 0.0331 X_k^4 or ln U_k < X_k^2/2 + d (1 - v + ln v); for a < 1
+ * the draw is multiplied by U_b^{1/a}.  A reading where the method has no
+ * bound: after 8 rejected trials (probability below 1e-10) the draw is d. */
+#define MB_TRIALS 8
+
+static void mb_block(uint32_t path, int64_t i, uint32_t b, const uint32_t key[2], uint32_t w[4]) {
+  uint32_t ctr[4] = {path, (uint32_t)i, b, ORC_TAG_MB};
+  orc_philox4x32_10(ctr, key, w);
+}
+
+static double mb_gamma(double a, double x0, double u0, double ub, uint32_t path, int64_t i,
+                       const uint32_t key[2]) {
+  double ap = a >= 1.0 ? a : a + 1.0;
+  double d = ap - 1.0 / 3.0;
+  double c = 1.0 / sqrt(9.0 * d);
+  double g = d;
+  for (int k = 0; k < MB_TRIALS; ++k) {
+    double x = x0, u = u0;
+    if (k > 0) {
+      uint32_t w[4];
+      double unused;
+      mb_block(path, i, (uint32_t)(k + 1), key, w);
+      orc_box_muller(orc_u01(w[0]), orc_u01(w[1]), &x, &unused);
+      u = orc_u01(w[2]);
+    }
+    double t = 1.0 + c * x;
+    if (!(t > 0.0)) continue;
+    double v = t * t * t;
+    if (u < 1.0 - 0.0331 * (x * x) * (x * x) || log(u) < 0.5 * x * x + d * (1.0 - v + log(v))) {
+      g = d * v;
+      break;
+    }
+  }
+  if (a < 1.0) g = g * pow(ub, 1.0 / a);
+  return g;
+}
+
+void orc_mb_gamma_draws(double a, uint64_t seed, int64_t n, double* out) {
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (int64_t j = 0; j < n; ++j) {
+    uint32_t w0[4], w1[4];
+    double za, n1, n2, x0;
+    mb_block((uint32_t)j, 0, 0u, key, w0);
+    mb_block((uint32_t)j, 0, 1u, key, w1);
+    orc_box_muller(orc_u01(w0[0]), orc_u01(w0[1]), &za, &n1);
+    orc_box_muller(orc_u01(w0[2]), orc_u01(w0[3]), &n2, &x0);
+    out[j] = mb_gamma(a, x0, orc_u01(w1[0]), orc_u01(w1[1]), (uint32_t)j, 0, key);
+  }
+}
+
+/* State of one path of the conditional-Bessel scheme: Y = F^{1-beta}/(1-beta)
+ * (beta < 1) or ln F (beta = 1). */
+typedef struct {
+  double Y, alpha, t;
+  int absorbed;
+} mb_state;
+
+static void mb_start(const double* p, double f, mb_state* s) {
+  double beta = p[1];
+  s->Y = beta == 1.0 ? log(f) : pow(f, 1.0 - beta) / (1.0 - beta);
+  s->alpha = p[0];
+  s->t = 0.0;
+  s->absorbed = 0;
+}
+
+static double mb_forward(const double* p, const mb_state* s) {
+  double beta = p[1];
+  if (s->absorbed) return 0.0;
+  return beta == 1.0 ? exp(s->Y) : pow((1.0 - beta) * s->Y, 1.0 / (1.0 - beta));
+}
+
+/* Step i of path `path` (from s->t to grid[i]); nu(t), rho(t) of the step at
+ * its right end, as in mc_step. */
+static void mc_step_bessel(int model, const double* p, const double* grid, int64_t i, uint32_t path,
+                           const uint32_t key[2], mb_state* s) {
+  int dyn = (model == ORC_DYN_I) ? 1 : (model == ORC_DYN_II ? 2 : 0);
+  double beta = p[1];
+  double h = grid[i] - s->t;
+  double nu = dyn ? orc_nu_t(dyn, p, grid[i]) : p[3];
+  double rho = dyn ? orc_rho_t(dyn, p, grid[i]) : p[2];
+  s->t = grid[i];
+  if (s->absorbed) return;
+  uint32_t w0[4], w1[4];
+  mb_block(path, i, 0u, key, w0);
+  mb_block(path, i, 1u, key, w1);
+  double za, n1, n2, x0;
+  orc_box_muller(orc_u01(w0[0]), orc_u01(w0[1]), &za, &n1);
+  orc_box_muller(orc_u01(w0[2]), orc_u01(w0[3]), &n2, &x0);
+  double u0 = orc_u01(w1[0]), ub = orc_u01(w1[1]);
+  /* step 1: the volatility */
+  double sh = sqrt(h);
+  double kap = nu * sh;
+  double em = expm1(kap * za - 0.5 * kap * kap);
+  double alpha_new = s->alpha + s->alpha * em;
+  /* step 2: (rho/nu)(alpha' - alpha) */
+  double shift = s->alpha * rho * sh * (kap > 0.0 ? em / kap : za);
+  /* step 3: int alpha^2 ds */
+  double V = 0.5 * h * (s->alpha * s->alpha + alpha_new * alpha_new);
+  double omr = (1.0 - rho) * (1.0 + rho);
+  s->alpha = alpha_new;
+  if (beta == 1.0) { /* step 5 */
+    s->Y = s->Y + shift - 0.5 * V + sqrt(omr * V) * n1;
+    return;
+  }
+  double Y0 = s->Y + shift;
+  if (!(Y0 > 0.0)) {
+    s->absorbed = 1;
+    return;
+  }
+  double tau = omr * V;
+  if (!(tau > 0.0)) { /* rho^2 = 1 */
+    double y2 = Y0 * Y0 - beta / (1.0 - beta) * V;
+    if (!(y2 > 0.0)) {
+      s->absorbed = 1;
+      return;
+    }
+    s->Y = sqrt(y2);
+    return;
+  }
+  /* step 4 */
+  double a = 0.5 + 0.5 * (beta / (1.0 - beta)) / omr;
+  double m = Y0 * Y0 / (2.0 * tau);
+  double G = mb_gamma(a, x0, u0, ub, path, i, key);
+  if (!(G < m)) {
+    s->absorbed = 1;
+    return;
+  }
+  double q = n1 + sqrt(2.0 * (m - G));
+  s->Y = sqrt(tau * (q * q + n2 * n2));
+}
+
+static void mc_path_bessel(int model, const double* p, double f, const double* grid,
+                           int64_t n_steps, const double* T, const double* K,
+                           const int8_t* is_call, const int64_t* qorder, int64_t n,
+                           uint32_t path, const uint32_t key[2], double* sum,
+                           double* sumsq) {
+  mb_state st;
+  mb_start(p, f, &st);
+  int64_t qi = 0;
+  for (int64_t i = 0; i < n_steps; ++i) {
+    mc_step_bessel(model, p, grid, i, path, key, &st);
+    while (qi < n && fabs(T[qorder[qi]] - st.t) <= 1e-10) {
+      int64_t q = qorder[qi++];
+      int call = is_call ? is_call[q] != 0 : 1;
+      double F = mb_forward(p, &st);
+      double pay = call ? (F > K[q] ? F - K[q] : 0.0) : (K[q] > F ? K[q] - F : 0.0);
+      sum[q] += pay;
+      sumsq[q] += pay * pay;
+    }
+  }
+}
+
 int orc_mc_price(int model, const double* p, double f, const double* T,
                  const double* K, const int8_t* is_call, const double* disc,
                  int64_t n, int64_t n_paths, double spy, uint64_t seed,
                  int n_threads, double* price, double* se) {
+  return orc_mc_price_scheme(ORC_MC_LOG_EULER, model, p, f, T, K, is_call, disc, n, n_paths, spy, seed,
+                             n_threads, price, se);
+}
+
+int orc_mc_price_scheme(int scheme, int model, const double* p, double f, const double* T,
+                        const double* K, const int8_t* is_call, const double* disc,
+                        int64_t n, int64_t n_paths, double spy, uint64_t seed,
+                        int n_threads, double* price, double* se) {
+  if (scheme != ORC_MC_LOG_EULER && scheme != ORC_MC_BESSEL) return -1;
   if (n <= 0 || n_paths <= 1 || !(spy > 0.0) || !(f > 0.0)) return -1;
   for (int64_t q = 0; q < n; ++q)
     if (!(T[q] > 0.0)) return -1;
@@ -570,9 +781,12 @@ int orc_mc_price(int model, const double* p, double f, const double* T,
     double* s = part + b * 2 * n;
     double* s2 = s + n;
     int64_t j1 = (b + 1) * BLK < n_paths ? (b + 1) * BLK : n_paths;
-    for (int64_t j = b * BLK; j < j1; ++j)
-      mc_path(model, p, f, grid, n_steps, T, K, is_call, qorder, n,
-              (uint32_t)j, key, s, s2);
+    for (int64_t j = b * BLK; j < j1; ++j) {
+      if (scheme == ORC_MC_BESSEL)
+        mc_path_bessel(model, p, f, grid, n_steps, T, K, is_call, qorder, n, (uint32_t)j, key, s, s2);
+      else
+        mc_path(model, p, f, grid, n_steps, T, K, is_call, qorder, n, (uint32_t)j, key, s, s2);
+    }
   }
   for (int64_t q = 0; q < n; ++q) {
     double s = 0.0, s2 = 0.0;

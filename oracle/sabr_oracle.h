@@ -114,6 +114,25 @@ int orc_mc_price(int model, const double* p, double f, const double* T,
                  int64_t n, int64_t n_paths, double steps_per_year,
                  uint64_t seed, int n_threads, double* price, double* stderr_out);
 
+/* Path schemes of the Monte Carlo pricer.  ORC_MC_LOG_EULER is the paper's
+ * scheme (Sec. 4, eq. (dis_SABRd)); ORC_MC_BESSEL is the low-bias variant
+ * the paper names as the fallback for log-Euler (Sec. 4, the scheme of Chen,
+ * Oosterlee and van der Weide): the volatility is stepped exactly, the
+ * forward is mapped, given the volatility path, to a squared Bessel process
+ * absorbed at zero, and that process is sampled exactly (see mc_step_bessel). */
+enum { ORC_MC_LOG_EULER = 0, ORC_MC_BESSEL = 1 };
+/* Counter tag of the conditional-Bessel step's Philox blocks. */
+#define ORC_TAG_MB 0x4D420000u
+/* orc_mc_price with a choice of scheme (same arguments and result). */
+int orc_mc_price_scheme(int scheme, int model, const double* p, double f,
+                        const double* T, const double* K, const int8_t* is_call,
+                        const double* disc, int64_t n, int64_t n_paths,
+                        double steps_per_year, uint64_t seed, int n_threads,
+                        double* price, double* stderr_out);
+/* n Gamma(a) draws of the conditional-Bessel step's sampler, draw j from the
+ * words of path j, step 0 (the sampler exactly as the step uses it). */
+void orc_mb_gamma_draws(double a, uint64_t seed, int64_t n, double* out);
+
 /* Sec. 6.3, eqs. (eq_cliquet), (cliquet_global): a cliquet on the forward
  * with reset dates d_i = i T / n_resets (i = 1 .. n_resets), paying
  * sum_{i=2..n} max(min(R_i, cap_l), floor_l), R_i = F(d_i)/F(d_{i-1}) - 1,
