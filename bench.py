@@ -316,6 +316,7 @@ def measure_mc(sg, torch, stream, rates, sm_mhz):
         out[name] = {"value": n_paths * steps / (ms / 1e3), "unit": "path-steps/s", "ms": ms}
     res = {"workload": "8 maturities x 15 strikes, 2^22 paths, %d steps, Hagan dynamics" % steps,
            "value": out["fp32"]["value"], "unit": "path-steps/s", "fp64_form": out["fp64"]}
+    res["bessel"] = measure_mc_bessel(sg, torch, stream, w, n_paths)
     if rates:
         peak, pipe, _ = pipe_bound(MC_STEP_OPS, rates, sm_mhz)
         res["roofline"] = {"bound": "alu", "pipe": pipe, "ops_per_path_step": MC_STEP_OPS,
@@ -334,6 +335,41 @@ def measure_mc(sg, torch, stream, rates, sm_mhz):
                                               "from": "ncu warp instructions x active lanes of the committed "
                                                       "2^20-path capture"}
     return res
+
+
+def measure_mc_bessel(sg, torch, stream, w, n_paths):
+    """The conditional-Bessel scheme (sabr_mc_price_scheme, SABR_MC_BESSEL)
+    on the same surface and paths, FP32: its path-step rate on the 250 steps
+    a year grid, and, against a log-Euler reference at 2000 steps a year, the
+    largest price bias of the Bessel scheme at 12 steps a year and of
+    log-Euler at 250 with the time each takes (independent streams; the
+    bias figures carry the reference's own noise, `reference_se_max`)."""
+    def timed(spy, scheme, seed):
+        sg.mc_price(sg.HAGAN, w.truth, 1.0, w.T, w.K, n_paths=1 << 16, steps_per_year=spy, seed=seed, scheme=scheme)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pr, se = sg.mc_price(sg.HAGAN, w.truth, 1.0, w.T, w.K, n_paths=n_paths, steps_per_year=spy, seed=seed,
+                             scheme=scheme)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b), pr.cpu().numpy(), se.cpu().numpy()
+    steps = grid_steps(w.T, 250.0)
+    ms250, _, _ = timed(250, sg.MC_BESSEL, 1)
+    _, ref, rse = timed(2000, None, 4)
+    ms12, p12, s12 = timed(12, sg.MC_BESSEL, 2)
+    msle, ple, sle = timed(250, None, 3)
+    return {"value": n_paths * steps / (ms250 / 1e3), "unit": "path-steps/s", "ms": ms250,
+            "workload": "the same surface and paths, %d steps (250 a year), FP32" % steps,
+            "equal_accuracy": {
+                "reference": "log-Euler at 2000 steps a year (%d steps)" % grid_steps(w.T, 2000.0),
+                "reference_se_max": float(np.max(rse)),
+                "bessel_12_per_year": {"steps": grid_steps(w.T, 12.0), "ms": ms12,
+                                       "max_abs_bias": float(np.max(np.abs(p12 - ref))),
+                                       "se_max": float(np.max(s12))},
+                "log_euler_250_per_year": {"steps": steps, "ms": msle,
+                                           "max_abs_bias": float(np.max(np.abs(ple - ref))),
+                                           "se_max": float(np.max(sle))},
+                "speedup": msle / ms12}}
 
 
 def measure_cliquet(sg, torch, stream, rates, sm_mhz):
@@ -643,7 +679,8 @@ def measure_serving_loads(sg, n_requests, fractions=(0.5, 0.8, 0.95), load_reque
 
 
 def run_mc_case():
-    """One sabr_mc_price on the MC surface shape at 2^20 paths (profiling)."""
+    """sabr_mc_price on the MC surface shape at 2^20 paths (profiling):
+    log-Euler FP32 twice, FP64, then the conditional-Bessel scheme FP32."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -652,6 +689,7 @@ def run_mc_case():
     w = workloads.mc_surface()
     for prec in (sg.FP32, sg.FP32, sg.FP64):
         sg.mc_price(sg.HAGAN, w.truth, 1.0, w.T, w.K, n_paths=1 << 20, steps_per_year=250, seed=1, prec=prec)
+    sg.mc_price(sg.HAGAN, w.truth, 1.0, w.T, w.K, n_paths=1 << 20, steps_per_year=250, seed=1, scheme=sg.MC_BESSEL)
     torch.cuda.synchronize()
     print(json.dumps({"case": "mc", "ok": True}))
 

@@ -64,6 +64,12 @@ typedef enum {
   SABR_FP64 = 1  /* FP64 throughout                                     */
 } sabr_precision;
 
+typedef enum {
+  SABR_MC_LOG_EULER = 0, /* Sec. 4, eq. (dis_SABRd): the paper's scheme     */
+  SABR_MC_BESSEL = 1     /* conditional-Bessel step: the low-bias fallback  */
+                         /* Sec. 4 names (see sabr_mc_price_scheme)         */
+} sabr_mc_scheme;
+
 /* ------------------------------------------------------------------------
  * sabr_implied_vol -- model implied volatility of n European options.
  * Sec. 2.1 eqs. (haganf), (sigma-SABR), (vola_SABR); Sec. 2.2 eq.
@@ -113,6 +119,37 @@ sabr_status sabr_mc_price(sabr_model model, const double* params, double fwd,
                           int64_t n, int64_t n_paths, double steps_per_year,
                           uint64_t seed, double* price_out, double* stderr_out,
                           sabr_precision prec, void* cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * sabr_mc_price_scheme -- sabr_mc_price with a choice of path scheme.  Same
+ * arguments, layout, ownership and checks; scheme SABR_MC_LOG_EULER gives
+ * exactly sabr_mc_price.  SABR_MC_BESSEL is the low-bias scheme Sec. 4 names
+ * as the fallback for log-Euler (after Chen, Oosterlee and van der Weide):
+ * per step, with nu(t), rho(t) at the step's right end,
+ *   - the vol moves exactly, alpha' = alpha exp(nu sqrt(h) Z - nu^2 h/2);
+ *   - rho int alpha dW = (rho/nu)(alpha' - alpha) is added to
+ *     Y = F^(1-beta)/(1-beta) at the start of the step;
+ *   - int alpha^2 ds is taken by the trapezoidal rule;
+ *   - given those, Y^2 is a squared Bessel process of dimension
+ *     1 - beta/((1-beta)(1-rho^2)) absorbed at 0 on the clock
+ *     (1-rho^2) int alpha^2 ds, sampled exactly (a Gamma draw by Marsaglia
+ *     and Tsang's method, then a noncentral chi-square with 2 degrees);
+ *   - beta = 1 steps ln F exactly given the vol path, without absorption.
+ * At nu = 0, rho = 0 the step is exact (the absorbed CEV law) at any step
+ * size; for nu > 0 a few steps a year match fine-grid log-Euler prices.
+ * Path j, step i draws Philox4x32-10 blocks (j, i, b, 0x4D420000), b = 0, 1
+ * always and b = 2 .. 8 for further Gamma trials.  A path is absorbed when
+ * its Bessel process reaches 0 (no 1e-12 threshold).  EINVAL for an
+ * unknown scheme and the checks of sabr_mc_price.
+ * ------------------------------------------------------------------------ */
+sabr_status sabr_mc_price_scheme(sabr_model model, const double* params,
+                                 double fwd, const double* T, const double* K,
+                                 const int8_t* is_call, const double* discount,
+                                 int64_t n, int64_t n_paths,
+                                 double steps_per_year, uint64_t seed,
+                                 sabr_mc_scheme scheme, double* price_out,
+                                 double* stderr_out, sabr_precision prec,
+                                 void* cuda_stream);
 
 /* ------------------------------------------------------------------------
  * sabr_mc_price_noalloc -- the same prices as sabr_mc_price, for callers

@@ -52,8 +52,10 @@ def implied_vol(model, params, fwd, T, K, prec=FP32, out=None, stream=None, devi
 
 
 def mc_price(model, params, fwd, T, K, is_call=None, discount=None, n_paths=1 << 16,
-             steps_per_year=250.0, seed=0, prec=FP32, stream=None, device="cuda"):
-    """Monte Carlo prices and standard errors (float64 CUDA tensors)."""
+             steps_per_year=250.0, seed=0, prec=FP32, stream=None, device="cuda", scheme=None):
+    """Monte Carlo prices and standard errors (float64 CUDA tensors).
+    scheme None: sabr_mc_price (log-Euler); capi.MC_LOG_EULER or
+    capi.MC_BESSEL: sabr_mc_price_scheme."""
     lib = capi.load()
     T = np.ascontiguousarray(T, dtype=np.float64).ravel()
     K = np.ascontiguousarray(np.broadcast_to(np.asarray(K, dtype=np.float64), T.shape))
@@ -62,13 +64,15 @@ def mc_price(model, params, fwd, T, K, is_call=None, discount=None, n_paths=1 <<
     price = torch.empty(T.size, dtype=torch.float64, device=device)
     se = torch.empty(T.size, dtype=torch.float64, device=device)
     p = _params10(params, model)
-    st = lib.sabr_mc_price(model, p.ctypes.data_as(capi.PD), float(fwd), T.ctypes.data_as(capi.PD),
-                           K.ctypes.data_as(capi.PD), ic.ctypes.data_as(capi.PI8) if ic is not None else None,
-                           dc.ctypes.data_as(capi.PD) if dc is not None else None, T.size, int(n_paths),
-                           float(steps_per_year), int(seed) & 0xFFFFFFFFFFFFFFFF,
-                           ctypes.c_void_p(price.data_ptr()), ctypes.c_void_p(se.data_ptr()), prec,
-                           _stream_handle(stream))
-    capi.check(st, "sabr_mc_price")
+    head = (model, p.ctypes.data_as(capi.PD), float(fwd), T.ctypes.data_as(capi.PD), K.ctypes.data_as(capi.PD),
+            ic.ctypes.data_as(capi.PI8) if ic is not None else None,
+            dc.ctypes.data_as(capi.PD) if dc is not None else None, T.size, int(n_paths), float(steps_per_year),
+            int(seed) & 0xFFFFFFFFFFFFFFFF)
+    tail = (ctypes.c_void_p(price.data_ptr()), ctypes.c_void_p(se.data_ptr()), prec, _stream_handle(stream))
+    if scheme is None:
+        capi.check(lib.sabr_mc_price(*head, *tail), "sabr_mc_price")
+    else:
+        capi.check(lib.sabr_mc_price_scheme(*head, int(scheme), *tail), "sabr_mc_price_scheme")
     return price, se
 
 

@@ -25,6 +25,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EAGAIN, EBUSY, ECANCELLED, ENOTFOUND = rang
 HAGAN, OBLOJ, EXPANDED, DYN_I, DYN_II = range(5)
 COST_VOL, COST_MC_PRICE = 0, 1
 FP32, FP64 = 0, 1
+MC_LOG_EULER, MC_BESSEL = 0, 1
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ETIMEOUT", "EAGAIN", "EBUSY", "ECANCELLED",
                 "ENOTFOUND"]
 MODEL_NAMES = {"hagan": HAGAN, "obloj": OBLOJ, "expanded": EXPANDED, "dyn1": DYN_I, "dyn2": DYN_II}
@@ -74,6 +75,8 @@ SIGNATURES = {
                                  c_void_p]),
     "sabr_mc_price": (c_int, [c_int, PD, c_double, PD, PD, PI8, PD, c_int64, c_int64, c_double, c_uint64,
                               c_void_p, c_void_p, c_int, c_void_p]),
+    "sabr_mc_price_scheme": (c_int, [c_int, PD, c_double, PD, PD, PI8, PD, c_int64, c_int64, c_double, c_uint64,
+                                     c_int, c_void_p, c_void_p, c_int, c_void_p]),
     "sabr_mc_price_noalloc": (c_int, [c_int, PD, c_double, PD, PD, PI8, PD, c_int64, c_int64, c_double,
                                       c_uint64, c_void_p, c_void_p, c_int, c_void_p]),
     "sabr_mc_cliquet": (c_int, [c_int, PD, c_double, c_double, c_int32, c_double, c_double, c_double, c_double,

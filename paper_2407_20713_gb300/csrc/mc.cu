@@ -7,6 +7,7 @@
 
 #include "common.h"
 #include "mc.cuh"
+#include "mc_bessel.cuh"
 #include "mc_host.h"
 
 namespace sabr {
@@ -47,8 +48,9 @@ __host__ __device__ inline McSmem mc_smem_layout(int n_steps, int n_quotes, int 
 // block0 + gridDim.x - 1 of a grid of grid_total blocks -- each block takes
 // the paths it would take in that grid -- and writes their partials at
 // positions 0 .. gridDim.x - 1; grid_total = 0 means the launch is the
-// whole grid.
-template <class R>
+// whole grid.  SCHEME: SABR_MC_LOG_EULER (eq. (dis_SABRd)) or
+// SABR_MC_BESSEL (the conditional-Bessel step of mc_bessel.cuh).
+template <class R, int SCHEME>
 __global__ void __launch_bounds__(kMcBlock) mc_paths_kernel(McDev P, const double* __restrict__ set_params,
                                                            const int* __restrict__ set_valid,
                                                            double* __restrict__ partial, int block0,
@@ -70,7 +72,11 @@ __global__ void __launch_bounds__(kMcBlock) mc_paths_kernel(McDev P, const doubl
   for (int i = 0; i < kMaxD; ++i) p[i] = set_params[(size_t)set * kMaxD + i];
   const int nv = P.n_slots * 32;
   for (int i = threadIdx.x; i < kMcWarps * nv; i += blockDim.x) wacc[i] = 0.0;
-  build_steps<R>(P, p, tab, land);
+  if constexpr (SCHEME == SABR_MC_BESSEL) {
+    build_steps_bessel<R>(P, p, (StepCoefB<R>*)tab, land);
+  } else {
+    build_steps<R>(P, p, tab, land);
+  }
   for (int q = threadIdx.x; q < P.n_quotes; q += blockDim.x) {
     sK[q] = (R)P.K[q];
     scall[q] = P.is_call[q];
@@ -83,9 +89,20 @@ __global__ void __launch_bounds__(kMcBlock) mc_paths_kernel(McDev P, const doubl
   __syncthreads();
   const int warp = threadIdx.x >> 5;
   const int64_t gblocks = grid_total > 0 ? grid_total : gridDim.x;
-  simulate_paths<R>(P, p, tab, land, s_q0, s_nq, s_slot, sK, scall,
-                    (int64_t)(block0 + blockIdx.x) * blockDim.x + threadIdx.x, gblocks * blockDim.x,
-                    wacc + (size_t)warp * nv);
+  const int64_t path0 = (int64_t)(block0 + blockIdx.x) * blockDim.x + threadIdx.x;
+  double* my_acc = wacc + (size_t)warp * nv;
+  if constexpr (SCHEME == SABR_MC_BESSEL) {
+    const StepCoefB<R>* tb = (const StepCoefB<R>*)tab;
+    if (p[1] == 1.0) {
+      simulate_paths_bessel<R, true>(P, p, tb, land, s_q0, s_nq, s_slot, sK, scall, path0, gblocks * blockDim.x,
+                                     my_acc);
+    } else {
+      simulate_paths_bessel<R, false>(P, p, tb, land, s_q0, s_nq, s_slot, sK, scall, path0, gblocks * blockDim.x,
+                                      my_acc);
+    }
+  } else {
+    simulate_paths<R>(P, p, tab, land, s_q0, s_nq, s_slot, sK, scall, path0, gblocks * blockDim.x, my_acc);
+  }
   __syncthreads();
   double* out = partial + ((size_t)set * gridDim.x + blockIdx.x) * nv;
   for (int v = threadIdx.x; v < nv; v += blockDim.x) {
@@ -256,9 +273,24 @@ void mc_fill_image(const McHost& h, unsigned char* host_img, unsigned char* dev_
   *disc = (double*)put(h.disc.data(), 8 * h.disc.size());
 }
 
-template <class R>
-static void set_mc_smem(size_t bytes) {
-  cudaFuncSetAttribute(mc_paths_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+using McPathsFn = void (*)(McDev, const double*, const int*, double*, int, int);
+
+// The path kernel of a problem's precision and scheme, with its dynamic
+// shared memory allowance raised to what the problem needs.
+static McPathsFn mc_paths_fn(const McHost& h) {
+  McPathsFn fn;
+  if (h.prec == SABR_FP64) {
+    fn = h.scheme == SABR_MC_BESSEL ? mc_paths_kernel<double, SABR_MC_BESSEL> : mc_paths_kernel<double, SABR_MC_LOG_EULER>;
+  } else {
+    fn = h.scheme == SABR_MC_BESSEL ? mc_paths_kernel<float, SABR_MC_BESSEL> : mc_paths_kernel<float, SABR_MC_LOG_EULER>;
+  }
+  cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h.smem);
+  return fn;
+}
+
+// Paths one thread takes at a time.
+static int mc_thread_paths(const McHost& h) {
+  return h.scheme == SABR_MC_BESSEL ? kBesselPathsPerThread : mc_paths_per_thread(h.prec);
 }
 
 // Blocks per parameter set.  Every block of a launch does the same work
@@ -271,17 +303,11 @@ static void set_mc_smem(size_t bytes) {
 // with a third of the GPU idle, 0.5).
 int mc_blocks_per_set(const McHost& h, int n_sets) {
   int per_sm = 8;
-  if (h.prec == SABR_FP64) {
-    set_mc_smem<double>(h.smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mc_paths_kernel<double>, kMcBlock, h.smem);
-  } else {
-    set_mc_smem<float>(h.smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mc_paths_kernel<float>, kMcBlock, h.smem);
-  }
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mc_paths_fn(h), kMcBlock, h.smem);
   per_sm = std::min(std::max(per_sm, 1), 8);
   const int64_t resident = device_sms() * (int64_t)per_sm;
   const int64_t sets = std::max(1, n_sets);
-  const int64_t per_block = (int64_t)kMcBlock * mc_paths_per_thread(h.prec);
+  const int64_t per_block = (int64_t)kMcBlock * mc_thread_paths(h);
   const int64_t by_paths = (h.n_paths + per_block - 1) / per_block;
   const int64_t p_max = std::max<int64_t>(1, std::min(by_paths, 8 * resident / sets));
   int64_t best = 1;
@@ -298,13 +324,7 @@ int mc_blocks_per_set(const McHost& h, int n_sets) {
 
 static void launch_paths(const McHost& h, const McDev& d, const double* set_params, const int* set_valid,
                          dim3 grid, double* partial, int block0, int grid_total, cudaStream_t s) {
-  if (h.prec == SABR_FP64) {
-    set_mc_smem<double>(h.smem);
-    mc_paths_kernel<double><<<grid, kMcBlock, h.smem, s>>>(d, set_params, set_valid, partial, block0, grid_total);
-  } else {
-    set_mc_smem<float>(h.smem);
-    mc_paths_kernel<float><<<grid, kMcBlock, h.smem, s>>>(d, set_params, set_valid, partial, block0, grid_total);
-  }
+  mc_paths_fn(h)<<<grid, kMcBlock, h.smem, s>>>(d, set_params, set_valid, partial, block0, grid_total);
 }
 
 sabr_status mc_launch(const McHost& h, const McDev& d, const double* set_params, const int* set_valid, int n_sets,
@@ -353,16 +373,18 @@ static sabr_status ensure_ws(McWorkspace& w, size_t dev_bytes, size_t host_bytes
 
 }  // namespace sabr
 
-extern "C" sabr_status sabr_mc_price(sabr_model model, const double* params, double fwd, const double* T,
-                                     const double* K, const int8_t* is_call, const double* discount, int64_t n,
-                                     int64_t n_paths, double steps_per_year, uint64_t seed, double* price_out,
-                                     double* stderr_out, sabr_precision prec, void* stream) {
-  using namespace sabr;
-  clear_error();
+namespace sabr {
+
+static sabr_status mc_price(sabr_model model, const double* params, double fwd, const double* T, const double* K,
+                            const int8_t* is_call, const double* discount, int64_t n, int64_t n_paths,
+                            double steps_per_year, uint64_t seed, int scheme, double* price_out, double* stderr_out,
+                            sabr_precision prec, void* stream) {
   SABR_TRY(check_params(model, params));
   if (!price_out) return fail(SABR_EINVAL, "price_out is NULL");
+  if (scheme != SABR_MC_LOG_EULER && scheme != SABR_MC_BESSEL) return fail(SABR_EINVAL, "unknown path scheme");
   McHost h;
   SABR_TRY(mc_prepare(model, fwd, T, K, is_call, discount, n, n_paths, steps_per_year, seed, prec, h));
+  h.scheme = scheme;
   if (model == SABR_DYN_II && !case2_feasible<double, double>(params, h.Tmax))
     return fail(SABR_EINVAL, "parameters violate rho(t) in [-1,1], nu(t) > 0");
   const int bps = mc_blocks_per_set(h, 1);
@@ -391,6 +413,27 @@ extern "C" sabr_status sabr_mc_price(sabr_model model, const double* params, dou
                      q_out, disc, price_out, stderr_out, (int)n, s));
   SABR_CUDA(cudaEventRecord(w.done, s));
   return SABR_OK;
+}
+
+}  // namespace sabr
+
+extern "C" sabr_status sabr_mc_price(sabr_model model, const double* params, double fwd, const double* T,
+                                     const double* K, const int8_t* is_call, const double* discount, int64_t n,
+                                     int64_t n_paths, double steps_per_year, uint64_t seed, double* price_out,
+                                     double* stderr_out, sabr_precision prec, void* stream) {
+  sabr::clear_error();
+  return sabr::mc_price(model, params, fwd, T, K, is_call, discount, n, n_paths, steps_per_year, seed,
+                        SABR_MC_LOG_EULER, price_out, stderr_out, prec, stream);
+}
+
+extern "C" sabr_status sabr_mc_price_scheme(sabr_model model, const double* params, double fwd, const double* T,
+                                            const double* K, const int8_t* is_call, const double* discount,
+                                            int64_t n, int64_t n_paths, double steps_per_year, uint64_t seed,
+                                            sabr_mc_scheme scheme, double* price_out, double* stderr_out,
+                                            sabr_precision prec, void* stream) {
+  sabr::clear_error();
+  return sabr::mc_price(model, params, fwd, T, K, is_call, discount, n, n_paths, steps_per_year, seed, (int)scheme,
+                        price_out, stderr_out, prec, stream);
 }
 
 // ---------------------------------------------------------------------------

@@ -11,6 +11,7 @@ namespace sabr {
 
 struct McHost {
   int model = 0, prec = 0, n_quotes = 0, n_steps = 0, n_slots = 0;
+  int scheme = SABR_MC_LOG_EULER;  // path scheme (sabr_mc_scheme)
   double fwd = 1.0, Tmax = 0.0;
   int64_t n_paths = 0;
   uint64_t seed = 0;
