@@ -231,6 +231,76 @@ __device__ __forceinline__ void case2_group_coef(const R* xp, int n_mats, R l2f,
   }
 }
 
+// Partial sum of the squared residuals of one lane's quotes, FP32 Hagan
+// form (quotes in pairs, SmemQuotes::pair): lane `lane` of G takes pairs
+// lane, lane + G, ...; an odd count's last quote belongs to lane
+// (full mod G) and joins the sum after the pairs.  With one lane per chain
+// the pairs run in straight-line chunks of PAIRS and the odd quote is
+// evaluated inside the first chunk, so that its dependency chain overlaps
+// the pairs' instead of running alone after them (measured +7.8% on the
+// 21-strike smiles, 2.53e10 -> 2.73e10 cost-evals/s); the order of the sum,
+// and so the result, is that of the strided loop.
+template <int PAIRS>
+__device__ __forceinline__ float hagan_partial(const StaticConst<float>& sc, int n_quotes,
+                                               const SmemQuotes<float>& sq, int lane, int G) {
+  const int full = n_quotes >> 1;  // pairs with two quotes
+  const bool odd = (n_quotes & 1) != 0;
+  auto pair_r = [&](int j) {
+    const float4 a = sq.pair[2 * j], b = sq.pair[2 * j + 1];
+    return hagan_resid_pair(sc, make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y),
+                            make_float2(b.z, b.w));
+  };
+  // the odd quote alone (the scalar form of the same formula)
+  auto odd_r = [&]() {
+    const float4 a = sq.pair[2 * full], b = sq.pair[2 * full + 1];
+    return fmaf(vol_hagan<float>(sc, a.x, a.z, b.x), b.z, 1.0f);
+  };
+  float2 acc2 = make_float2(0.0f, 0.0f);
+  float r_odd = 0.0f;
+  bool odd_here;
+  if (G == 1) {
+    odd_here = odd;
+    int j = 0;
+    if (full >= PAIRS) {
+      float2 r[PAIRS];
+      if (odd) {
+#pragma unroll
+        for (int k = 0; k < PAIRS; ++k) r[k] = pair_r(k);
+        r_odd = odd_r();
+      } else {
+#pragma unroll
+        for (int k = 0; k < PAIRS; ++k) r[k] = pair_r(k);
+      }
+#pragma unroll
+      for (int k = 0; k < PAIRS; ++k) acc2 = fma2(r[k], r[k], acc2);
+      j = PAIRS;
+    } else if (odd) {
+      r_odd = odd_r();
+    }
+    for (; j + PAIRS <= full; j += PAIRS) {
+      float2 r[PAIRS];
+#pragma unroll
+      for (int k = 0; k < PAIRS; ++k) r[k] = pair_r(j + k);
+#pragma unroll
+      for (int k = 0; k < PAIRS; ++k) acc2 = fma2(r[k], r[k], acc2);
+    }
+    for (; j < full; ++j) {
+      const float2 r = pair_r(j);
+      acc2 = fma2(r, r, acc2);
+    }
+  } else {
+    odd_here = odd && (full & (G - 1)) == lane;
+#pragma unroll PAIRS
+    for (int j = lane; j < full; j += G) {
+      const float2 r = pair_r(j);
+      acc2 = fma2(r, r, acc2);
+    }
+    if (odd_here) r_odd = odd_r();
+  }
+  if (odd_here) acc2.x = fmaf(r_odd, r_odd, acc2.x);
+  return acc2.x + acc2.y;
+}
+
 // The Hagan cost of two points at once (the speculative step loop of the
 // level kernel): every lane evaluates its quotes for both points, with the
 // lane assignment, order of summation and arithmetic of group_cost for each
@@ -423,22 +493,7 @@ __device__ __forceinline__ typename CostOf<R>::T group_cost(const R* xp, int n_q
   R acc = (R)0;
   if constexpr (MODEL == SABR_HAGAN && sizeof(R) == 4) {
     const StaticConst<float> sc = static_setup<float>(xp);
-    float2 acc2 = make_float2(0.0f, 0.0f);
-    const int full = n_quotes >> 1;  // pairs with two quotes
-#pragma unroll PAIRS
-    for (int j = lane; j < full; j += G) {
-      const float4 a = sq.pair[2 * j], b = sq.pair[2 * j + 1];
-      const float2 r = hagan_resid_pair(sc, make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y),
-                                        make_float2(b.z, b.w));
-      acc2 = fma2(r, r, acc2);
-    }
-    if ((n_quotes & 1) && (full & (G - 1)) == lane) {
-      // an odd count's last quote, alone (the scalar form of the same formula)
-      const float4 a = sq.pair[2 * full], b = sq.pair[2 * full + 1];
-      const float r = fmaf(vol_hagan<float>(sc, a.x, a.z, b.x), b.z, 1.0f);
-      acc2.x = fmaf(r, r, acc2.x);
-    }
-    acc = acc2.x + acc2.y;
+    acc = hagan_partial<PAIRS>(sc, n_quotes, sq, lane, G);
   } else if (MODEL == SABR_HAGAN || MODEL == SABR_OBLOJ) {
     const StaticConst<R> sc = static_setup<R>(xp);
 #pragma unroll 3
