@@ -532,6 +532,18 @@ def measure_dynamic(sg, torch, stream, levels=N_LEVELS, rates=None, sm_mhz=None)
                 "bound": "alu", "pipe": pipe, "unit": "cost-evals/s", "peak": peak,
                 "achieved": r.n_evals / (ms / 1e3), "frac": r.n_evals / (ms / 1e3) / peak,
                 "ops_per_proposal": DYN_PROPOSAL_OPS[case]}
+            # the ceiling the kernel meets: issue slots, at the instructions
+            # per proposal drawn (out-of-box and infeasible ones included)
+            # of the committed one-level capture of the same surface
+            ti = profiled_thread_instructions("sa_level_kernel_dyn%d_joint_surface.md" % case, LEVEL_KERNEL_SOURCES)
+            if ti:
+                per_unit = ti / (w.n_chains * CHAIN_LEN)
+                ib = issue_bound(per_unit, sm_mhz)
+                drawn = w.n_chains * CHAIN_LEN * levels / (ms / 1e3)
+                res["case%d" % case]["roofline"]["issue_bound"] = {
+                    "unit": "proposals drawn/s", "thread_instructions_per_unit": per_unit, "peak": ib,
+                    "achieved": drawn, "frac": drawn / ib,
+                    "from": "ncu warp instructions x active lanes of the committed one-level capture"}
         plan.close()
     return res
 
