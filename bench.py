@@ -143,10 +143,12 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the MC, dynamic and serving measurements")
     ap.add_argument("--levels", type=int, default=None,
                     help="temperature levels of the headline surface (default 200; fewer for a short ncu capture)")
-    ap.add_argument("--case", choices=["full", "small", "mc", "cliquet", "dynamic1", "dynamic2"], default="full",
+    ap.add_argument("--case", choices=["full", "small", "mc", "cliquet", "dynamic1", "dynamic2", "single"],
+                    default="full",
                     help="small: 2 smiles x 10 levels, main measurement only; mc: one 2^20-path MC pricing "
                          "of the MC surface; cliquet: one 2^20-path cliquet; dynamic1 / dynamic2: two runs of "
-                         "three levels of the joint Case I / Case II fit (the last five for profiler captures)")
+                         "three levels of the joint Case I / Case II fit; single: two FP32 calibrations of the "
+                         "one-smile configuration (the last six for profiler captures)")
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-loads", type=float, nargs="*", default=[0.5, 0.8, 0.95],
                     help="fractions of capacity for --serve-only (each with --serve-requests requests)")
@@ -728,6 +730,28 @@ def run_dynamic_case(case):
     print(json.dumps({"case": "dynamic%d" % case, "ok": True}))
 
 
+def run_single_case():
+    """Two FP32 calibrations of one Hagan smile (15 strikes, 64 chains,
+    200 levels x 100 proposals) as one plan (profiling)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2407_20713_gb300 as sg
+    from paper_2407_20713_gb300 import workloads
+    w = workloads.one_smile()
+    mkt = sg.implied_vol(sg.HAGAN, w.truth, 1.0, w.T, w.K, prec=sg.FP64).cpu().numpy() + w.noise
+    pb = sg.CalibrationProblem(model=sg.HAGAN, T=w.T, K=w.K, market=mkt, lo=w.lo, hi=w.hi, prec=sg.FP32,
+                               n_chains=w.n_chains, n_levels=N_LEVELS, chain_len=CHAIN_LEN, factor=FACTOR, seed=1)
+    plan = sg.Plan([pb], use_graph=True)
+    for _ in range(2):
+        plan.run(torch.cuda.current_stream())
+        plan.results()
+    n_launch, _ = plan.stats()
+    plan.close()
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "single", "ok": True, "launches_per_run": n_launch}))
+
+
 def run_cliquet_case():
     """One sabr_mc_cliquet of the Sec. 6.3 contract at 2^20 paths (profiling)."""
     import torch
@@ -948,6 +972,8 @@ if __name__ == "__main__":
         run_mc_case()
     elif a.case == "cliquet":
         run_cliquet_case()
+    elif a.case == "single":
+        run_single_case()
     elif a.case in ("dynamic1", "dynamic2"):
         run_dynamic_case(int(a.case[-1]))
     else:

@@ -233,13 +233,13 @@ __device__ __forceinline__ void case2_group_coef(const R* xp, int n_mats, R l2f,
 
 // Partial sum of the squared residuals of one lane's quotes, FP32 Hagan
 // form (quotes in pairs, SmemQuotes::pair): lane `lane` of G takes pairs
-// lane, lane + G, ...; an odd count's last quote belongs to lane
-// (full mod G) and joins the sum after the pairs.  With one lane per chain
+// lane, lane + G, ... (an odd count's last quote in its zero-filled pair).
+// With one lane per chain
 // the pairs run in straight-line chunks of PAIRS and the odd quote is
 // evaluated inside the first chunk, so that its dependency chain overlaps
 // the pairs' instead of running alone after them (measured +7.8% on the
-// 21-strike smiles, 2.53e10 -> 2.73e10 cost-evals/s); the order of the sum,
-// and so the result, is that of the strided loop.
+// 21-strike smiles, 2.53e10 -> 2.73e10 cost-evals/s); its residual joins
+// the sum after the pairs.
 template <int PAIRS>
 __device__ __forceinline__ float hagan_partial(const StaticConst<float>& sc, int n_quotes,
                                                const SmemQuotes<float>& sq, int lane, int G) {
@@ -289,63 +289,74 @@ __device__ __forceinline__ float hagan_partial(const StaticConst<float>& sc, int
       acc2 = fma2(r, r, acc2);
     }
   } else {
-    odd_here = odd && (full & (G - 1)) == lane;
+    // several lanes: an odd count's last quote is evaluated as the first
+    // element of its zero-filled pair (residual 0 for the filler), so the
+    // lane that holds it runs the same instructions as the others instead
+    // of a separate scalar pass while they wait
+    odd_here = false;
+    const int npairs = full + (odd ? 1 : 0);
 #pragma unroll PAIRS
-    for (int j = lane; j < full; j += G) {
-      const float2 r = pair_r(j);
+    for (int j = lane; j < npairs; j += G) {
+      const float4 a = sq.pair[2 * j], b = sq.pair[2 * j + 1];
+      const float2 r = hagan_resid_pair(sc, make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y),
+                                        make_float2(b.z, b.w), make_float2(1.0f, 2 * j + 1 < n_quotes ? 1.0f : 0.0f));
       acc2 = fma2(r, r, acc2);
     }
-    if (odd_here) r_odd = odd_r();
   }
   if (odd_here) acc2.x = fmaf(r_odd, r_odd, acc2.x);
   return acc2.x + acc2.y;
 }
 
-// The Hagan cost of two points at once (the speculative step loop of the
-// level kernel): every lane evaluates its quotes for both points, with the
-// lane assignment, order of summation and arithmetic of group_cost for each
-// point, so each result equals group_cost's bit for bit; the two evaluations
-// are independent work for the scheduler.
-template <class R, int PAIRS>
-__device__ __forceinline__ void group_cost2_hagan(const R* xa, const R* xb, int n_quotes,
-                                                  const SmemQuotes<R>& sq, int lane, int G, unsigned gmask,
-                                                  typename CostOf<R>::T& fa, typename CostOf<R>::T& fb) {
-  R acc_a = (R)0, acc_b = (R)0;
+// The Hagan cost of SD points at once (the speculative step loop of the
+// level kernel): every lane evaluates its quotes for each point, with the
+// lane assignment, order of summation and arithmetic of group_cost for
+// each point, so each result equals group_cost's bit for bit; the SD
+// evaluations are independent work for the scheduler.
+template <class R, int PAIRS, int SD>
+__device__ __forceinline__ void group_costn_hagan(const R (&xs)[SD][4], int n_quotes, const SmemQuotes<R>& sq,
+                                                  int lane, int G, unsigned gmask,
+                                                  typename CostOf<R>::T (&fs)[SD]) {
+  R acc[SD];
   if constexpr (sizeof(R) == 4) {
-    const StaticConst<float> sa = static_setup<float>(xa), sb = static_setup<float>(xb);
+    StaticConst<float> sc[SD];
+#pragma unroll
+    for (int k = 0; k < SD; ++k) sc[k] = static_setup<float>(xs[k]);
     const int full = n_quotes >> 1;
-    float2 a2 = make_float2(0.0f, 0.0f), b2 = make_float2(0.0f, 0.0f);
+    const int npairs = full + (n_quotes & 1);
+    float2 a2[SD];
+#pragma unroll
+    for (int k = 0; k < SD; ++k) a2[k] = make_float2(0.0f, 0.0f);
 #pragma unroll PAIRS
-    for (int j = lane; j < full; j += G) {
+    for (int j = lane; j < npairs; j += G) {
       const float4 a = sq.pair[2 * j], b = sq.pair[2 * j + 1];
       const float2 lfk = make_float2(a.x, a.y), l2kf = make_float2(a.z, a.w), T = make_float2(b.x, b.y),
-                   wn = make_float2(b.z, b.w);
-      const float2 ra = hagan_resid_pair(sa, lfk, l2kf, T, wn);
-      const float2 rb = hagan_resid_pair(sb, lfk, l2kf, T, wn);
-      a2 = fma2(ra, ra, a2);
-      b2 = fma2(rb, rb, b2);
+                   wn = make_float2(b.z, b.w), one = make_float2(1.0f, 2 * j + 1 < n_quotes ? 1.0f : 0.0f);
+#pragma unroll
+      for (int k = 0; k < SD; ++k) {
+        const float2 r = hagan_resid_pair(sc[k], lfk, l2kf, T, wn, one);
+        a2[k] = fma2(r, r, a2[k]);
+      }
     }
-    if ((n_quotes & 1) && (full & (G - 1)) == lane) {
-      const float4 a = sq.pair[2 * full], b = sq.pair[2 * full + 1];
-      const float ra = fmaf(vol_hagan<float>(sa, a.x, a.z, b.x), b.z, 1.0f);
-      const float rb = fmaf(vol_hagan<float>(sb, a.x, a.z, b.x), b.z, 1.0f);
-      a2.x = fmaf(ra, ra, a2.x);
-      b2.x = fmaf(rb, rb, b2.x);
-    }
-    acc_a = a2.x + a2.y;
-    acc_b = b2.x + b2.y;
+#pragma unroll
+    for (int k = 0; k < SD; ++k) acc[k] = a2[k].x + a2[k].y;
   } else {
-    const StaticConst<R> sa = static_setup<R>(xa), sb = static_setup<R>(xb);
+    StaticConst<R> sc[SD];
+#pragma unroll
+    for (int k = 0; k < SD; ++k) {
+      sc[k] = static_setup<R>(xs[k]);
+      acc[k] = (R)0;
+    }
     for (int q = lane; q < n_quotes; q += G) {
       const QuotePack<R> qp = sq.pack[q];
-      const R ra = resid(vol_hagan<R>(sa, qp.lfk, qp.l2kf, qp.T), qp.w);
-      const R rb = resid(vol_hagan<R>(sb, qp.lfk, qp.l2kf, qp.T), qp.w);
-      acc_a += ra * ra;
-      acc_b += rb * rb;
+#pragma unroll
+      for (int k = 0; k < SD; ++k) {
+        const R r = resid(vol_hagan<R>(sc[k], qp.lfk, qp.l2kf, qp.T), qp.w);
+        acc[k] += r * r;
+      }
     }
   }
-  fa = lanes_sum(acc_a, G, gmask);
-  fb = lanes_sum(acc_b, G, gmask);
+#pragma unroll
+  for (int k = 0; k < SD; ++k) fs[k] = lanes_sum(acc[k], G, gmask);
 }
 
 // FP32 Case II: the four functions of eq. (integrales_SABRd) of every

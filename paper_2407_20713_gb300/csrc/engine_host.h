@@ -34,7 +34,7 @@ sabr_status formula_prepare(const sabr_problem& pr, const sabr_bounds& b, const 
 // Tuning override: the environment variable SABR_LANES (a power of two in
 // [1, 32]) sets it for every problem; results then differ only by the FP32
 // rounding of the lane sums.
-int choose_lanes(int n_quotes, int n_mats, int model, long long batch_chains);
+int choose_lanes(int n_quotes, int n_mats, int model, int prec, long long batch_chains);
 // Dynamic shared memory of a level block (cpb chains) / of an init block;
 // c2_nsub: sub-panels of the FP32 Case II rule (0 otherwise).
 size_t level_smem_bytes(int prec, int model, int Q, int M, int cpb, int c2_nsub = 0);

@@ -105,11 +105,15 @@ __device__ __forceinline__ void warp_argmin(double& f, int& i) {
   }
 }
 
-// Quote pairs per point the speculative Hagan loop keeps in flight (two
-// points are evaluated at once, so fewer than QueuePairs).
+// Quote pairs per point the speculative Hagan loop keeps in flight (several
+// points are evaluated at once, so fewer than QueuePairs), and the steps it
+// evaluates at once: two (on one 15-strike smile, 64 chains, 8 lanes a
+// chain, four measured 8% slower: 17.39 against 16.12 ms per calibration;
+// the results do not depend on the depth).
 template <class R> struct SpecPairs {
   static constexpr int value = 2;
 };
+constexpr int kSpecDepth = 2;
 
 template <int MODEL> struct Dim {
   static constexpr int value = MODEL == SABR_DYN_II ? 10 : (MODEL == SABR_DYN_I ? 6 : 4);
@@ -317,93 +321,92 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int pid, int
     if constexpr (MODEL == SABR_HAGAN) {
       if (P.spec) {
         // Speculative acceptance (Hagan, several lanes per chain).
-        // Acceptance is the common outcome (with T0 = f(x0) about 95% of
-        // the proposals on the benchmark surfaces), so each iteration forms
-        // step st's proposal xa from x
-        // and step st+1's proposal xb from xa, as if xa were accepted, and
-        // evaluates both (group_cost2_hagan: per point the arithmetic and
-        // order of group_cost).  If step st accepts, step st+1 is decided
-        // with xb's cost and the chain advances two steps; otherwise xb is
-        // dropped and step st+1 is drawn again from x.  The trajectory,
+        // Acceptance is the common outcome (about 96% of the evaluated
+        // proposals on the benchmark smiles), so each iteration forms step
+        // st's proposal from x and the proposal of each step st + k
+        // (k < SD) from that of step st + k - 1, as if every earlier one
+        // were accepted, and evaluates all SD points at once
+        // (group_costn_hagan: per point the arithmetic and order of
+        // group_cost).  The steps are then decided in order with these
+        // costs until one is rejected (out of the box, NaN or by the
+        // Metropolis test): that step still counts, the later points are
+        // dropped, and the chain advances past it.  The trajectory,
         // counters and best point are those of the one-step loop below.
         ran_spec = true;
+        constexpr int SD = kSpecDepth;
         auto words = [&](int s) { return draw(make_uint4(gchain, (uint32_t)level, (uint32_t)s, kTagSA)); };
-        uint4 w0 = words(0), w1 = words(1);
+        uint4 w[SD];
+#pragma unroll
+        for (int k = 0; k < SD; ++k) w[k] = words(k);
         int st = 0;
         while (st < P.chain_len) {
-          const uint4 w2 = words(st + 2), w3 = words(st + 3);  // off the critical path
-          R ua[D + 1], ub[D + 1];
-          ua[0] = u01<R>(w0.x);
-          ua[1] = u01<R>(w0.y);
-          ua[2] = u01<R>(w0.z);
-          ua[3] = u01<R>(w0.w);
-          ua[D] = u01<R>(sa_accept_word(w0.x, w0.y, w0.z));
-          ub[0] = u01<R>(w1.x);
-          ub[1] = u01<R>(w1.y);
-          ub[2] = u01<R>(w1.z);
-          ub[3] = u01<R>(w1.w);
-          ub[D] = u01<R>(sa_accept_word(w1.x, w1.y, w1.z));
-          R xa[D], xb[D];
-          bool in_a = true, in_b = true;
+          // the words of the next SD steps, should all SD be taken (off the
+          // critical path)
+          uint4 wn[SD];
 #pragma unroll
-          for (int i = 0; i < D; ++i) {
-            xa[i] = propose(x[i], s_step[i], ua[i]);
-            in_a = in_a && !(xa[i] < s_lo[i] || xa[i] > s_hi[i]);
-            xb[i] = propose(xa[i], s_step[i], ub[i]);
-            in_b = in_b && !(xb[i] < s_lo[i] || xb[i] > s_hi[i]);
+          for (int k = 0; k < SD; ++k) wn[k] = words(st + SD + k);
+          R u[SD][D + 1];
+          R xs[SD][4];
+          bool in[SD];
+#pragma unroll
+          for (int k = 0; k < SD; ++k) {
+            u[k][0] = u01<R>(w[k].x);
+            u[k][1] = u01<R>(w[k].y);
+            u[k][2] = u01<R>(w[k].z);
+            u[k][3] = u01<R>(w[k].w);
+            u[k][D] = u01<R>(sa_accept_word(w[k].x, w[k].y, w[k].z));
+            in[k] = true;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+              xs[k][i] = propose(k == 0 ? x[i] : xs[k - 1][i], s_step[i], u[k][i]);
+              in[k] = in[k] && !(xs[k][i] < s_lo[i] || xs[k][i] > s_hi[i]);
+            }
           }
           int adv = 1;
-          if (in_a) {
-            C fa, fb;
-            group_cost2_hagan<R, SpecPairs<R>::value>(xa, xb, P.n_quotes, sq, lane, G, gmask, fa, fb);
-            ++ev;
-            bool acc_a = false;
-            if (!cost_is_nan(fa)) {
-              if (cost_less(fa, bf)) {
-                bf = fa;
-                if (lane == 0) {
+          if (in[0]) {
+            C f[SD];
+            group_costn_hagan<R, SpecPairs<R>::value, SD>(xs, P.n_quotes, sq, lane, G, gmask, f);
+            bool go = true;
 #pragma unroll
-                  for (int i = 0; i < D; ++i) cbx[i] = xa[i];
-                }
-              }
-              const auto da = cost_delta(fa, fcur);
-              acc_a = da <= 0 || metropolis(ua[D], da, inv_Tk, Tk);
-            }
-            if (acc_a) {
-#pragma unroll
-              for (int i = 0; i < D; ++i) x[i] = xa[i];
-              fcur = fa;
-              ++ac;
-              if (st + 1 < P.chain_len) {
-                adv = 2;
-                if (in_b) {
+            for (int k = 0; k < SD; ++k) {
+              if (go && st + k < P.chain_len) {
+                adv = k + 1;
+                bool acc = false;
+                if (in[k]) {
                   ++ev;
-                  if (!cost_is_nan(fb)) {
-                    if (cost_less(fb, bf)) {
-                      bf = fb;
+                  if (!cost_is_nan(f[k])) {
+                    if (cost_less(f[k], bf)) {
+                      bf = f[k];
                       if (lane == 0) {
 #pragma unroll
-                        for (int i = 0; i < D; ++i) cbx[i] = xb[i];
+                        for (int i = 0; i < D; ++i) cbx[i] = xs[k][i];
                       }
                     }
-                    const auto db = cost_delta(fb, fcur);
-                    if (db <= 0 || metropolis(ub[D], db, inv_Tk, Tk)) {
-#pragma unroll
-                      for (int i = 0; i < D; ++i) x[i] = xb[i];
-                      fcur = fb;
-                      ++ac;
-                    }
+                    const auto dk = cost_delta(f[k], fcur);
+                    acc = dk <= 0 || metropolis(u[k][D], dk, inv_Tk, Tk);
                   }
+                }
+                if (acc) {
+#pragma unroll
+                  for (int i = 0; i < D; ++i) x[i] = xs[k][i];
+                  fcur = f[k];
+                  ++ac;
+                } else {
+                  go = false;
                 }
               }
             }
           }
-          if (adv == 1) {
-            w0 = w1;
-            w1 = w2;
-          } else {
-            w0 = w2;
-            w1 = w3;
+          // words of the next iteration's steps st + adv .. st + adv + SD - 1
+          // from the current and the next window
+#pragma unroll
+          for (int k = 0; k < SD; ++k) {
+            uint4 v = wn[k];  // adv == SD
+#pragma unroll
+            for (int a = 1; a < SD; ++a) {
+              if (adv == a) v = k + a < SD ? w[k + a] : wn[k + a - SD];
+            }
+            w[k] = v;
           }
           st += adv;
         }
@@ -788,7 +791,7 @@ static int next_pow2(int v) {
 // time), widened while the batch has fewer than (SMs x 256) threads and quotes
 // remain to split; the dynamic models take one lane per two maturities and
 // per ~48 quotes.
-int choose_lanes(int n_quotes, int n_mats, int model, long long batch_chains) {
+int choose_lanes(int n_quotes, int n_mats, int model, int prec, long long batch_chains) {
   if (const char* e = std::getenv("SABR_LANES")) {
     int g = std::atoi(e);
     if (g >= 1 && g <= 32 && (g & (g - 1)) == 0) return g;
@@ -804,7 +807,11 @@ int choose_lanes(int n_quotes, int n_mats, int model, long long batch_chains) {
   if (model == SABR_DYN_I || model == SABR_DYN_II)
     G = std::max(std::max(1, next_pow2(n_mats) / 2), next_pow2((n_quotes + 47) / 48));
   G = std::min(G, 32);
-  const int cap = std::min(32, next_pow2(n_quotes));
+  // the FP32 Hagan form hands its lanes pairs of quotes (more lanes than
+  // pairs would idle; on one 15-strike smile, 64 chains: 8 lanes 16.12 ms,
+  // 16 lanes 16.50 ms per calibration)
+  const int units = (model == SABR_HAGAN && prec == SABR_FP32) ? (n_quotes + 1) / 2 : n_quotes;
+  const int cap = std::min(32, next_pow2(units));
   const long long fill = (long long)device_sms() * 256;
   while (G < cap && batch_chains * G < fill) G <<= 1;
   return G;
@@ -1309,7 +1316,7 @@ static sabr_status build_plan(int32_t n, const sabr_problem* problems, const sab
   const size_t results_off = take(sizeof(sabr_result) * n);
   std::vector<size_t> f_off(nf), mc_off(p->mc.size());
   for (int i = 0; i < nf; ++i) {
-    lanes[i] = choose_lanes(hp[i].n_quotes, hp[i].n_mats, hp[i].model, batch_chains);
+    lanes[i] = choose_lanes(hp[i].n_quotes, hp[i].n_mats, hp[i].model, hp[i].prec, batch_chains);
     if (level_smem_bytes(hp[i].prec, hp[i].model, hp[i].n_quotes, hp[i].n_mats, kLevelBlock / lanes[i],
                          hp[i].c2_nsub) > kMaxLevelSmem) {
       free_plan(p);
@@ -1356,12 +1363,19 @@ static sabr_status build_plan(int32_t n, const sabr_problem* problems, const sab
     }
     // The queue pays when a level of the group has more units than the
     // persistent grid has blocks and several problems can fill each
-    // other's level ends; a single problem (every unit of a level waits for
-    // the same restart point) runs level by level.
+    // other's level ends.  A single problem (every unit of a level waits for
+    // the same restart point) uses it only when two of its levels fit in the
+    // persistent grid: the grid then holds the blocks of one level and, on
+    // the queue, those of the next, which start as soon as the level closes
+    // instead of after a kernel launch (a level's fixed cost on one smile of
+    // 64 chains: 13.7 us with a launch per level); larger single problems
+    // run level by level.
     const int per_sm = std::min(workers_per_sm(g.prec, g.model), queue_blocks_per_sm(g.prec, g.model, g.smem_level));
-    const int grid = std::max(1, std::min(g.total_blocks, sms * per_sm));
-    g.use_queue = queue_enabled() && g.problems.size() > 1 && g.total_blocks > grid && nf <= kQueueMaxProblems &&
-                  p->max_levels < kQueueMaxLevels && total * 8 <= kMaxQueueBytes;
+    int grid = std::max(1, std::min(g.total_blocks, sms * per_sm));
+    const bool single_small = g.problems.size() == 1 && 2 * g.total_blocks <= sms * per_sm && p->max_levels > 1;
+    if (single_small) grid = 2 * g.total_blocks;
+    g.use_queue = queue_enabled() && ((g.problems.size() > 1 && g.total_blocks > grid) || single_small) &&
+                  nf <= kQueueMaxProblems && p->max_levels < kQueueMaxLevels && total * 8 <= kMaxQueueBytes;
     for (int pi : g.problems) g.use_queue = g.use_queue && pd[pi].n_blocks <= kQueueMaxBlocks;
     if (g.use_queue) {
       g.q.total = total;

@@ -430,8 +430,9 @@ __device__ __forceinline__ R vol_hagan(const StaticConst<R>& s, R lfk, R l2kf, R
 // multiplies per quote take half the issue slots of the scalar form; the
 // SFU operations and the branch selects stay per element.  Same operations,
 // in the same order and contraction, as vol_hagan<float> with
-// z_over_x_parts<float>; returns the residuals r = 1 + v * (-1/market) of
-// both quotes.
+// z_over_x_parts<float>; returns the residuals r = one + v * (-1/market) of
+// both quotes (one = 1, or 0 for the zero-filled second element of an odd
+// count's last pair, whose residual is then exactly 0).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -439,7 +440,7 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
 __device__ __forceinline__ float2 hagan_resid_pair(const StaticConst<float>& s, float2 lfk, float2 l2kf, float2 T,
-                                                   float2 wneg) {
+                                                   float2 wneg, float2 one = make_float2(1.0f, 1.0f)) {
   const float2 e = mul2(f2(s.half_omb), l2kf);
   const float2 fk = make_float2(ex2_approx(e.x), ex2_approx(e.y));
   const float2 L2 = mul2(lfk, lfk);
@@ -468,7 +469,7 @@ __device__ __forceinline__ float2 hagan_resid_pair(const StaticConst<float>& s, 
   const float2 num = fma2(fk2, fma2(f2(s.abr_c), T, f2(s.alpha)), mul2(fma2(f2(s.abr_b), fk, f2(s.abr_a)), T));
   const float2 dd = mul2(mul2(mul2(fk2, fk), den), xd);
   const float2 v = mul2(mul2(zn, num), make_float2(rcp_approx(dd.x), rcp_approx(dd.y)));
-  return fma2(v, wneg, f2(1.0f));
+  return fma2(v, wneg, one);
 }
 
 template <class R>

@@ -483,7 +483,7 @@ static sabr_status submit(sabr_server* s, const sabr_problem* pr, const sabr_bou
   } else {
     SABR_TRY(formula_prepare(*pr, *b, *c, seed, r->hp));
     if (r->hp.n_quotes > s->cfg.max_quotes) return fail(SABR_EINVAL, "request has more quotes than max_quotes");
-    r->G = choose_lanes(r->hp.n_quotes, r->hp.n_mats, r->hp.model, r->hp.n_chains);
+    r->G = choose_lanes(r->hp.n_quotes, r->hp.n_mats, r->hp.model, r->hp.prec, r->hp.n_chains);
     ProblemDev tmp;
     r->bytes = formula_layout(r->hp, r->G, nullptr, nullptr, 0, tmp, nullptr) + 256;
     r->n_blocks = tmp.n_blocks;

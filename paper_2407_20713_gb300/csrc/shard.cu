@@ -58,7 +58,7 @@ static sabr_status shard_create(const sabr_problem* pr, const sabr_bounds* b, co
     return e;
   }
   // lanes per chain as for the whole problem calibrated alone
-  const int G = choose_lanes(s->hp.n_quotes, s->hp.n_mats, s->hp.model, s->hp.n_chains);
+  const int G = choose_lanes(s->hp.n_quotes, s->hp.n_mats, s->hp.model, s->hp.prec, s->hp.n_chains);
   s->hp.n_chains = chain_count;
   s->hp.chain0 = chain_begin;
   if (level_smem_bytes(s->hp.prec, s->hp.model, s->hp.n_quotes, s->hp.n_mats, kLevelBlock / G, s->hp.c2_nsub) >

@@ -152,7 +152,7 @@ def test_ready_queue_equals_level_by_level_launches(monkeypatch):
     mkt = market()
     T, K, mk2, lo2, hi2 = dyn_surface(O.DYN_I)
     pbs = [sg.CalibrationProblem(model=sg.HAGAN, T=T15, K=K15, market=mkt, lo=LO4, hi=HI4, prec=sg.FP32,
-                                 n_chains=3000, n_levels=12, chain_len=20, seed=31),
+                                 n_chains=6000, n_levels=12, chain_len=20, seed=31),
            sg.CalibrationProblem(model=sg.HAGAN, T=T15[:9], K=K15[:9], market=mkt[:9], lo=LO4, hi=HI4,
                                  prec=sg.FP32, n_chains=700, n_levels=5, chain_len=20, seed=32),
            sg.CalibrationProblem(model=sg.DYN_I, T=T, K=K, market=mk2, lo=lo2, hi=hi2, prec=sg.FP64,
@@ -166,8 +166,9 @@ def test_ready_queue_equals_level_by_level_launches(monkeypatch):
     plan.close()
     # FP32 Hagan group (three problems, more units per level than resident
     # blocks): init, queue reset, one persistent launch, finalize; the FP64
-    # Case I group (one problem): init, 7 levels, finalize
-    assert n_launch == 2 + 2 + 7 + 2
+    # Case I group (one problem, two of whose levels fit in the persistent
+    # grid): the same four launches
+    assert n_launch == 2 + 2 + 2 + 2
     monkeypatch.setenv("SABR_PLAN_QUEUE", "0")
     plan = sg.Plan(pbs, use_graph=True)
     plan.run()
@@ -422,8 +423,8 @@ def test_fp32_in_loop_cost_matches_the_oracle(model, truth, lo, hi, mats):
 
 @pytest.mark.parametrize("prec", [sg.FP32, sg.FP64])
 def test_speculative_hagan_loop_equals_the_one_step_loop(prec, monkeypatch):
-    # Hagan chains with several lanes evaluate step st and, as if it were
-    # accepted, step st+1 together; the results (best point, restart point,
+    # Hagan chains with several lanes evaluate step st and, as if each were
+    # accepted, the next steps together; the results (best point, restart point,
     # misfits, counters) must be those of the one-step loop bit for bit,
     # for small problems whose lanes share the quotes (the large batch, one
     # lane per chain, runs the one-step loop either way)
@@ -434,9 +435,13 @@ def test_speculative_hagan_loop_equals_the_one_step_loop(prec, monkeypatch):
                                  n_chains=4000, n_levels=6, chain_len=31, seed=41 + i) for i in range(3)]
     small = sg.CalibrationProblem(model=sg.HAGAN, T=T15, K=K15, market=mkt, lo=LO4, hi=HI4, prec=prec,
                                   n_chains=48, n_levels=8, chain_len=40, seed=44)
-    spec = sg.calibrate_batch(pbs) + [sg.calibrate(small)]
+    # chain lengths shorter than, and not a multiple of, the speculation depth
+    short = [sg.CalibrationProblem(model=sg.HAGAN, T=T15[:8], K=K15[:8], market=mkt[:8], lo=LO4, hi=HI4,
+                                   prec=prec, n_chains=20, n_levels=5, chain_len=cl, seed=45 + cl)
+             for cl in (1, 2, 3, 5, 7)]
+    spec = sg.calibrate_batch(pbs) + [sg.calibrate(small)] + [sg.calibrate(q) for q in short]
     monkeypatch.setenv("SABR_SPECULATE", "0")
-    plain = sg.calibrate_batch(pbs) + [sg.calibrate(small)]
+    plain = sg.calibrate_batch(pbs) + [sg.calibrate(small)] + [sg.calibrate(q) for q in short]
     for a, b in zip(spec, plain):
         assert a.status == b.status == 0
         assert np.array_equal(a.params, b.params) and np.array_equal(a.restart_params, b.restart_params)
