@@ -307,6 +307,48 @@ __device__ __forceinline__ float hagan_partial(const StaticConst<float>& sc, int
   return acc2.x + acc2.y;
 }
 
+// The FP32 Hagan cost with one lane per chain and at least PAIRS pairs,
+// for a step loop specialised to that case (and to the parity of the quote
+// count, ODD): the static constants of the point, the first chunk of pairs
+// and the odd quote form one straight-line block, so the constants'
+// dependency chain (a reciprocal and two logarithms) overlaps the chunk's
+// first pairs.  Same operations and order of summation as group_cost at
+// G = 1 (hagan_partial), so the same result bit for bit.
+template <int PAIRS, bool ODD>
+__device__ __forceinline__ DF hagan_cost_g1(const float* xp, int n_quotes, const SmemQuotes<float>& sq) {
+  const StaticConst<float> sc = static_setup<float>(xp);
+  const int full = n_quotes >> 1;
+  auto pair_r = [&](int j) {
+    const float4 a = sq.pair[2 * j], b = sq.pair[2 * j + 1];
+    return hagan_resid_pair(sc, make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y),
+                            make_float2(b.z, b.w));
+  };
+  float2 r[PAIRS];
+#pragma unroll
+  for (int k = 0; k < PAIRS; ++k) r[k] = pair_r(k);
+  float r_odd = 0.0f;
+  if constexpr (ODD) {
+    const float4 a = sq.pair[2 * full], b = sq.pair[2 * full + 1];
+    r_odd = fmaf(vol_hagan<float>(sc, a.x, a.z, b.x), b.z, 1.0f);
+  }
+  float2 acc2 = make_float2(0.0f, 0.0f);
+#pragma unroll
+  for (int k = 0; k < PAIRS; ++k) acc2 = fma2(r[k], r[k], acc2);
+  int j = PAIRS;
+  for (; j + PAIRS <= full; j += PAIRS) {
+#pragma unroll
+    for (int k = 0; k < PAIRS; ++k) r[k] = pair_r(j + k);
+#pragma unroll
+    for (int k = 0; k < PAIRS; ++k) acc2 = fma2(r[k], r[k], acc2);
+  }
+  for (; j < full; ++j) {
+    const float2 q = pair_r(j);
+    acc2 = fma2(q, q, acc2);
+  }
+  if constexpr (ODD) acc2.x = fmaf(r_odd, r_odd, acc2.x);
+  return DF{acc2.x + acc2.y, 0.0f};
+}
+
 // The Hagan cost of SD points at once (the speculative step loop of the
 // level kernel): every lane evaluates its quotes for each point, with the
 // lane assignment, order of summation and arithmetic of group_cost for

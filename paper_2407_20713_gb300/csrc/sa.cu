@@ -114,6 +114,9 @@ template <class R> struct SpecPairs {
   static constexpr int value = 2;
 };
 constexpr int kSpecDepth = 2;
+template <int N> struct IntTag {
+  static constexpr int value = N;
+};
 
 template <int MODEL> struct Dim {
   static constexpr int value = MODEL == SABR_DYN_II ? 10 : (MODEL == SABR_DYN_I ? 6 : 4);
@@ -412,86 +415,110 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int pid, int
         }
       }
     }
-    uint4 wbuf = make_uint4(0u, 0u, 0u, 0u);
-    constexpr int NB = sa_philox_blocks(D);  // Philox blocks per step
-    const int S = G >= NB ? G / NB : 1;  // steps per batch of Philox blocks
-    int s_ctr = 0;                         // st mod S
-    uint4 wnext = make_uint4(0u, 0u, 0u, 0u);
-    if (NB == 1 && G == 1 && !ran_spec)
-      wnext = draw(make_uint4(gchain, (uint32_t)level, 0u, kTagSA));
-    for (int st = 0; st < (ran_spec ? 0 : P.chain_len); ++st) {
-      // D Philox words of blocks 0, 1, ... with counter (chain, level, step,
-      // tag + block): D move uniforms and, from their unused low bits, the
-      // acceptance uniform (sa_accept_word).  With G >= NB lanes, the chain's
-      // lanes compute the blocks of S = G/NB consecutive steps at once
-      // (lane l: step st0 + l/NB, block l%NB) and every step gathers its
-      // words by shuffles; otherwise each lane computes all NB blocks of
-      // every step.
-      uint32_t wv[4 * NB];
-      if (NB == 1 && G == 1) {
-        // one lane, one block: no exchange; the block of the next step is
-        // formed here, off the critical path of this one (its counter does
-        // not depend on this step's outcome)
-        const uint4 w = wnext;
-        wnext = draw(make_uint4(gchain, (uint32_t)level, (uint32_t)(st + 1), kTagSA));
-        wv[0] = w.x;
-        wv[1] = w.y;
-        wv[2] = w.z;
-        wv[3] = w.w;
-      } else if (G >= NB) {
-        const int s_in = s_ctr;
-        s_ctr = s_ctr + 1 == S ? 0 : s_ctr + 1;
-        if (s_in == 0) {
-          const int l = lane < S * NB ? lane : 0;
-          wbuf = draw(make_uint4(gchain, (uint32_t)level, (uint32_t)(st + l / NB), kTagSA + (uint32_t)(l % NB)));
+    // The step loop; KIND 1 / 2: FP32 Hagan, one lane per chain, at least
+    // PAIRS pairs, an even / odd quote count (hagan_cost_g1), else 0 (the
+    // choice is made once per unit, outside the loop, so the loop body
+    // holds no branch on it).
+    auto step_loop = [&](auto kind) {
+      constexpr int KIND = decltype(kind)::value;
+      uint4 wbuf = make_uint4(0u, 0u, 0u, 0u);
+      constexpr int NB = sa_philox_blocks(D);  // Philox blocks per step
+      const int S = G >= NB ? G / NB : 1;  // steps per batch of Philox blocks
+      int s_ctr = 0;                         // st mod S
+      uint4 wnext = make_uint4(0u, 0u, 0u, 0u);
+      if (NB == 1 && G == 1 && !ran_spec)
+        wnext = draw(make_uint4(gchain, (uint32_t)level, 0u, kTagSA));
+      for (int st = 0; st < (ran_spec ? 0 : P.chain_len); ++st) {
+        // D Philox words of blocks 0, 1, ... with counter (chain, level, step,
+        // tag + block): D move uniforms and, from their unused low bits, the
+        // acceptance uniform (sa_accept_word).  With G >= NB lanes, the chain's
+        // lanes compute the blocks of S = G/NB consecutive steps at once
+        // (lane l: step st0 + l/NB, block l%NB) and every step gathers its
+        // words by shuffles; otherwise each lane computes all NB blocks of
+        // every step.
+        uint32_t wv[4 * NB];
+        if (NB == 1 && G == 1) {
+          // one lane, one block: no exchange; the block of the next step is
+          // formed here, off the critical path of this one (its counter does
+          // not depend on this step's outcome)
+          const uint4 w = wnext;
+          wnext = draw(make_uint4(gchain, (uint32_t)level, (uint32_t)(st + 1), kTagSA));
+          wv[0] = w.x;
+          wv[1] = w.y;
+          wv[2] = w.z;
+          wv[3] = w.w;
+        } else if (G >= NB) {
+          const int s_in = s_ctr;
+          s_ctr = s_ctr + 1 == S ? 0 : s_ctr + 1;
+          if (s_in == 0) {
+            const int l = lane < S * NB ? lane : 0;
+            wbuf = draw(make_uint4(gchain, (uint32_t)level, (uint32_t)(st + l / NB), kTagSA + (uint32_t)(l % NB)));
+          }
+          const int base = ((threadIdx.x & 31) & ~(G - 1)) + s_in * NB;
+  #pragma unroll
+          for (int i = 0; i < D; ++i) {
+            const uint32_t word =
+                (i & 3) == 0 ? wbuf.x : ((i & 3) == 1 ? wbuf.y : ((i & 3) == 2 ? wbuf.z : wbuf.w));
+            wv[i] = __shfl_sync(gmask, word, base + (i >> 2));
+          }
+        } else {
+  #pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            const uint4 w = draw(make_uint4(gchain, (uint32_t)level, (uint32_t)st, kTagSA + (uint32_t)b));
+            wv[4 * b + 0] = w.x;
+            wv[4 * b + 1] = w.y;
+            wv[4 * b + 2] = w.z;
+            wv[4 * b + 3] = w.w;
+          }
         }
-        const int base = ((threadIdx.x & 31) & ~(G - 1)) + s_in * NB;
-#pragma unroll
+        R u[D + 1];
+  #pragma unroll
+        for (int i = 0; i < D; ++i) u[i] = u01<R>(wv[i]);
+        u[D] = u01<R>(sa_accept_word(wv[0], wv[1], wv[2]));
+        R xp[D];
+        bool inside = true;
+  #pragma unroll
         for (int i = 0; i < D; ++i) {
-          const uint32_t word =
-              (i & 3) == 0 ? wbuf.x : ((i & 3) == 1 ? wbuf.y : ((i & 3) == 2 ? wbuf.z : wbuf.w));
-          wv[i] = __shfl_sync(gmask, word, base + (i >> 2));
+          xp[i] = propose(x[i], s_step[i], u[i]);
+          inside = inside && !(xp[i] < s_lo[i] || xp[i] > s_hi[i]);
         }
+        if (MODEL == SABR_DYN_II && inside) inside = case2_feasible<R>(xp, Tmax);
+        if (!inside) continue;
+        C fp;
+        if constexpr (KIND == 0) {
+          fp = group_cost<R, MODEL, PAIRS>(xp, P.n_quotes, P.n_mats, l2f, sq, coef, lane, G, gmask);
+        } else {
+          fp = hagan_cost_g1<PAIRS, KIND == 2>(xp, P.n_quotes, sq);
+        }
+        ++ev;
+        if (cost_is_nan(fp)) continue;
+        if (cost_less(fp, bf)) {
+          bf = fp;
+          if (lane == 0) {
+  #pragma unroll
+            for (int i = 0; i < D; ++i) cbx[i] = xp[i];
+          }
+        }
+        const auto delta = cost_delta(fp, fcur);
+        if (delta <= 0 || metropolis(u[D], delta, inv_Tk, Tk)) {
+  #pragma unroll
+          for (int i = 0; i < D; ++i) x[i] = xp[i];
+          fcur = fp;
+          ++ac;
+        }
+      }
+    };
+    if constexpr (MODEL == SABR_HAGAN && sizeof(R) == 4) {
+      const bool one_lane = !ran_spec && G == 1 && (P.n_quotes >> 1) >= PAIRS;
+      if (one_lane && (P.n_quotes & 1)) {
+        step_loop(IntTag<2>{});
+      } else if (one_lane) {
+        step_loop(IntTag<1>{});
       } else {
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-          const uint4 w = draw(make_uint4(gchain, (uint32_t)level, (uint32_t)st, kTagSA + (uint32_t)b));
-          wv[4 * b + 0] = w.x;
-          wv[4 * b + 1] = w.y;
-          wv[4 * b + 2] = w.z;
-          wv[4 * b + 3] = w.w;
-        }
+        step_loop(IntTag<0>{});
       }
-      R u[D + 1];
-#pragma unroll
-      for (int i = 0; i < D; ++i) u[i] = u01<R>(wv[i]);
-      u[D] = u01<R>(sa_accept_word(wv[0], wv[1], wv[2]));
-      R xp[D];
-      bool inside = true;
-#pragma unroll
-      for (int i = 0; i < D; ++i) {
-        xp[i] = propose(x[i], s_step[i], u[i]);
-        inside = inside && !(xp[i] < s_lo[i] || xp[i] > s_hi[i]);
-      }
-      if (MODEL == SABR_DYN_II && inside) inside = case2_feasible<R>(xp, Tmax);
-      if (!inside) continue;
-      const C fp = group_cost<R, MODEL, PAIRS>(xp, P.n_quotes, P.n_mats, l2f, sq, coef, lane, G, gmask);
-      ++ev;
-      if (cost_is_nan(fp)) continue;
-      if (cost_less(fp, bf)) {
-        bf = fp;
-        if (lane == 0) {
-#pragma unroll
-          for (int i = 0; i < D; ++i) cbx[i] = xp[i];
-        }
-      }
-      const auto delta = cost_delta(fp, fcur);
-      if (delta <= 0 || metropolis(u[D], delta, inv_Tk, Tk)) {
-#pragma unroll
-        for (int i = 0; i < D; ++i) x[i] = xp[i];
-        fcur = fp;
-        ++ac;
-      }
+    } else {
+      step_loop(IntTag<0>{});
     }
     if (lane == 0) {
       P.chain_bf[chain] = cost_to_double(bf);
