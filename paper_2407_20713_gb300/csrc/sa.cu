@@ -455,14 +455,14 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int pid, int
             wbuf = draw(make_uint4(gchain, (uint32_t)level, (uint32_t)(st + l / NB), kTagSA + (uint32_t)(l % NB)));
           }
           const int base = ((threadIdx.x & 31) & ~(G - 1)) + s_in * NB;
-  #pragma unroll
+#pragma unroll
           for (int i = 0; i < D; ++i) {
             const uint32_t word =
                 (i & 3) == 0 ? wbuf.x : ((i & 3) == 1 ? wbuf.y : ((i & 3) == 2 ? wbuf.z : wbuf.w));
             wv[i] = __shfl_sync(gmask, word, base + (i >> 2));
           }
         } else {
-  #pragma unroll
+#pragma unroll
           for (int b = 0; b < NB; ++b) {
             const uint4 w = draw(make_uint4(gchain, (uint32_t)level, (uint32_t)st, kTagSA + (uint32_t)b));
             wv[4 * b + 0] = w.x;
@@ -472,12 +472,12 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int pid, int
           }
         }
         R u[D + 1];
-  #pragma unroll
+#pragma unroll
         for (int i = 0; i < D; ++i) u[i] = u01<R>(wv[i]);
         u[D] = u01<R>(sa_accept_word(wv[0], wv[1], wv[2]));
         R xp[D];
         bool inside = true;
-  #pragma unroll
+#pragma unroll
         for (int i = 0; i < D; ++i) {
           xp[i] = propose(x[i], s_step[i], u[i]);
           inside = inside && !(xp[i] < s_lo[i] || xp[i] > s_hi[i]);
@@ -495,13 +495,13 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int pid, int
         if (cost_less(fp, bf)) {
           bf = fp;
           if (lane == 0) {
-  #pragma unroll
+#pragma unroll
             for (int i = 0; i < D; ++i) cbx[i] = xp[i];
           }
         }
         const auto delta = cost_delta(fp, fcur);
         if (delta <= 0 || metropolis(u[D], delta, inv_Tk, Tk)) {
-  #pragma unroll
+#pragma unroll
           for (int i = 0; i < D; ++i) x[i] = xp[i];
           fcur = fp;
           ++ac;
