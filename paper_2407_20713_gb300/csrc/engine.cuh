@@ -240,20 +240,20 @@ __device__ __forceinline__ void case2_group_coef(const R* xp, int n_mats, R l2f,
 // the pairs' instead of running alone after them (measured +7.8% on the
 // 21-strike smiles, 2.53e10 -> 2.73e10 cost-evals/s); its residual joins
 // the sum after the pairs.
-template <int PAIRS>
-__device__ __forceinline__ float hagan_partial(const StaticConst<float>& sc, int n_quotes,
+template <int PAIRS, bool T1>
+__device__ __forceinline__ float hagan_partial(const StaticConst<float>& sc, const HaganT1& h, int n_quotes,
                                                const SmemQuotes<float>& sq, int lane, int G) {
   const int full = n_quotes >> 1;  // pairs with two quotes
   const bool odd = (n_quotes & 1) != 0;
   auto pair_r = [&](int j) {
     const float4 a = sq.pair[2 * j], b = sq.pair[2 * j + 1];
-    return hagan_resid_pair(sc, make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y),
-                            make_float2(b.z, b.w));
+    return hagan_resid_pair<T1>(sc, make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y),
+                                make_float2(b.z, b.w), make_float2(1.0f, 1.0f), h);
   };
   // the odd quote alone (the scalar form of the same formula)
   auto odd_r = [&]() {
     const float4 a = sq.pair[2 * full], b = sq.pair[2 * full + 1];
-    return fmaf(vol_hagan<float>(sc, a.x, a.z, b.x), b.z, 1.0f);
+    return fmaf(vol_hagan_f32<T1>(sc, h, a.x, a.z, b.x), b.z, 1.0f);
   };
   float2 acc2 = make_float2(0.0f, 0.0f);
   float r_odd = 0.0f;
@@ -298,8 +298,9 @@ __device__ __forceinline__ float hagan_partial(const StaticConst<float>& sc, int
 #pragma unroll PAIRS
     for (int j = lane; j < npairs; j += G) {
       const float4 a = sq.pair[2 * j], b = sq.pair[2 * j + 1];
-      const float2 r = hagan_resid_pair(sc, make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y),
-                                        make_float2(b.z, b.w), make_float2(1.0f, 2 * j + 1 < n_quotes ? 1.0f : 0.0f));
+      const float2 r = hagan_resid_pair<T1>(sc, make_float2(a.x, a.y), make_float2(a.z, a.w),
+                                            make_float2(b.x, b.y), make_float2(b.z, b.w),
+                                            make_float2(1.0f, 2 * j + 1 < n_quotes ? 1.0f : 0.0f), h);
       acc2 = fma2(r, r, acc2);
     }
   }
@@ -314,14 +315,15 @@ __device__ __forceinline__ float hagan_partial(const StaticConst<float>& sc, int
 // dependency chain (a reciprocal and two logarithms) overlaps the chunk's
 // first pairs.  Same operations and order of summation as group_cost at
 // G = 1 (hagan_partial), so the same result bit for bit.
-template <int PAIRS, bool ODD>
+template <int PAIRS, bool ODD, bool T1>
 __device__ __forceinline__ DF hagan_cost_g1(const float* xp, int n_quotes, const SmemQuotes<float>& sq) {
   const StaticConst<float> sc = static_setup<float>(xp);
+  const HaganT1 h = T1 ? hagan_t1(sc, sq.mT[0]) : HaganT1{0.0f, 0.0f, 0.0f};
   const int full = n_quotes >> 1;
   auto pair_r = [&](int j) {
     const float4 a = sq.pair[2 * j], b = sq.pair[2 * j + 1];
-    return hagan_resid_pair(sc, make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y),
-                            make_float2(b.z, b.w));
+    return hagan_resid_pair<T1>(sc, make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y),
+                                make_float2(b.z, b.w), make_float2(1.0f, 1.0f), h);
   };
   float2 r[PAIRS];
 #pragma unroll
@@ -329,7 +331,7 @@ __device__ __forceinline__ DF hagan_cost_g1(const float* xp, int n_quotes, const
   float r_odd = 0.0f;
   if constexpr (ODD) {
     const float4 a = sq.pair[2 * full], b = sq.pair[2 * full + 1];
-    r_odd = fmaf(vol_hagan<float>(sc, a.x, a.z, b.x), b.z, 1.0f);
+    r_odd = fmaf(vol_hagan_f32<T1>(sc, h, a.x, a.z, b.x), b.z, 1.0f);
   }
   float2 acc2 = make_float2(0.0f, 0.0f);
 #pragma unroll
@@ -546,7 +548,13 @@ __device__ __forceinline__ typename CostOf<R>::T group_cost(const R* xp, int n_q
   R acc = (R)0;
   if constexpr (MODEL == SABR_HAGAN && sizeof(R) == 4) {
     const StaticConst<float> sc = static_setup<float>(xp);
-    acc = hagan_partial<PAIRS>(sc, n_quotes, sq, lane, G);
+    // one lane per chain and one maturity: the folded numerator (HaganT1),
+    // as in the one-lane step loop (hagan_cost_g1)
+    if (G == 1 && n_mats == 1) {
+      acc = hagan_partial<PAIRS, true>(sc, hagan_t1(sc, sq.mT[0]), n_quotes, sq, lane, G);
+    } else {
+      acc = hagan_partial<PAIRS, false>(sc, HaganT1{0.0f, 0.0f, 0.0f}, n_quotes, sq, lane, G);
+    }
   } else if (MODEL == SABR_HAGAN || MODEL == SABR_OBLOJ) {
     const StaticConst<R> sc = static_setup<R>(xp);
 #pragma unroll 3

@@ -439,8 +439,42 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
+// Per-proposal constants of eq. (haganf) for quotes of one maturity T (a
+// problem whose quotes all share T, such as one smile): the bracket's T
+// terms folded into the numerator, num = fk (fk A + B) + C with
+// A = alpha + alpha br_c T, B = alpha br_b T, C = alpha br_a T (two FP32x2
+// operations fewer per pair of quotes).
+struct HaganT1 {
+  float A, B, C;
+};
+__device__ __forceinline__ HaganT1 hagan_t1(const StaticConst<float>& s, float T) {
+  return HaganT1{fmaf(s.abr_c, T, s.alpha), s.abr_b * T, s.abr_a * T};
+}
+
+// One quote of eq. (haganf) in FP32: vol_hagan<float>, or with the
+// numerator of HaganT1 when T1 (T is then not read).
+template <bool T1>
+__device__ __forceinline__ float vol_hagan_f32(const StaticConst<float>& s, const HaganT1& h, float lfk, float l2kf,
+                                               float T) {
+  if constexpr (!T1) {
+    return vol_hagan<float>(s, lfk, l2kf, T);
+  } else {
+    const float fk = ex2_approx(s.half_omb * l2kf);
+    const float L2 = lfk * lfk;
+    const float den = 1.0f + L2 * (s.c2 + s.c4 * L2);
+    const float z = s.nu_over_alpha * lfk * fk;
+    float zn, xd;
+    z_over_x_parts<float>(z, s.zx, zn, xd);
+    const float fk2 = fk * fk;
+    const float num = fmaf(fk, fmaf(fk, h.A, h.B), h.C);
+    return m_div(zn * num, fk2 * fk * den * xd);
+  }
+}
+
+template <bool T1 = false>
 __device__ __forceinline__ float2 hagan_resid_pair(const StaticConst<float>& s, float2 lfk, float2 l2kf, float2 T,
-                                                   float2 wneg, float2 one = make_float2(1.0f, 1.0f)) {
+                                                   float2 wneg, float2 one = make_float2(1.0f, 1.0f),
+                                                   const HaganT1& h = HaganT1{0.0f, 0.0f, 0.0f}) {
   const float2 e = mul2(f2(s.half_omb), l2kf);
   const float2 fk = make_float2(ex2_approx(e.x), ex2_approx(e.y));
   const float2 L2 = mul2(lfk, lfk);
@@ -466,7 +500,12 @@ __device__ __forceinline__ float2 hagan_resid_pair(const StaticConst<float>& s, 
   const float2 xd = make_float2(fabsf(nx ? S2.x : ax.x), fabsf(ny ? S2.y : ax.y));
   // sigma = (z/x) [fk^2 (alpha + alpha br_c T) + (alpha br_b fk + alpha br_a) T] / (fk^3 den)
   const float2 fk2 = mul2(fk, fk);
-  const float2 num = fma2(fk2, fma2(f2(s.abr_c), T, f2(s.alpha)), mul2(fma2(f2(s.abr_b), fk, f2(s.abr_a)), T));
+  float2 num;
+  if constexpr (T1) {
+    num = fma2(fk, fma2(fk, f2(h.A), f2(h.B)), f2(h.C));
+  } else {
+    num = fma2(fk2, fma2(f2(s.abr_c), T, f2(s.alpha)), mul2(fma2(f2(s.abr_b), fk, f2(s.abr_a)), T));
+  }
   const float2 dd = mul2(mul2(mul2(fk2, fk), den), xd);
   const float2 v = mul2(mul2(zn, num), make_float2(rcp_approx(dd.x), rcp_approx(dd.y)));
   return fma2(v, wneg, one);

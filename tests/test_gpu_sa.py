@@ -159,6 +159,13 @@ def test_ready_queue_equals_level_by_level_launches(monkeypatch):
                                  n_chains=90, n_levels=7, chain_len=10, seed=33),
            sg.CalibrationProblem(model=sg.HAGAN, T=T15, K=K15, market=mkt, lo=LO4, hi=HI4, prec=sg.FP32,
                                  n_chains=64, n_levels=0, chain_len=20, seed=34)]
+    # 21 and 20 strikes, enough chains for one lane per chain: the step
+    # loops with a first chunk of ten pairs, odd and even quote counts
+    K21 = 0.5 + 0.05 * np.arange(21)
+    m21 = market(T=np.ones(21), K=K21, seed=5)
+    pbs += [sg.CalibrationProblem(model=sg.HAGAN, T=np.ones(n), K=K21[:n], market=m21[:n], lo=LO4, hi=HI4,
+                                  prec=sg.FP32, n_chains=20000, n_levels=6, chain_len=20, seed=35 + n)
+            for n in (21, 20)]
     plan = sg.Plan(pbs, use_graph=True)
     plan.run()
     queued = plan.results()
