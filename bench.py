@@ -564,12 +564,17 @@ def measure_serving(sg, n_requests, rate_hz, formula_only=False):
         sm = q.smile
         if q.cost == 0:
             mkt = sg.implied_vol(sm.model, sm.truth, 1.0, sm.T, sm.K, prec=sg.FP64).cpu().numpy() + sm.noise
+            # the asymptotic formulas can give a non-positive vol at extreme
+            # synthetic truths (one Case II request of the 10 000-request
+            # stream, 3 of its 55 quotes): such quotes are left out, as a
+            # market would not quote them
+            keep = np.isfinite(mkt) & (mkt > 0.0)
         else:
             mkt = sg.mc_price(sm.model, sm.truth, 1.0, sm.T, sm.K, n_paths=q.mc_paths, steps_per_year=250,
                               seed=99)[0].cpu().numpy()
             # quotes priced below 1e-6 f are left out of a price calibration
             keep = mkt >= 1e-6
-            sm.T, sm.K, mkt = sm.T[keep], sm.K[keep], mkt[keep]
+        sm.T, sm.K, mkt = sm.T[keep], sm.K[keep], mkt[keep]
         probs.append(sg.CalibrationProblem(model=sm.model, T=sm.T, K=sm.K, market=mkt, lo=sm.lo, hi=sm.hi,
                                            cost=q.cost, prec=sg.FP32, n_chains=sm.n_chains, n_levels=q.n_levels,
                                            chain_len=q.chain_len, mc_paths=max(q.mc_paths, 2),
