@@ -368,10 +368,14 @@ sabr_status sabr_plan_results(sabr_plan* plan, sabr_result* out);
 /* Kernel launches one run of the plan enqueues, and the average time of one
  * temperature level (all problems of the plan) over the last run, from
  * events around the level work (ms; 0 if not timed).  The levels of a
- * launch group run in one persistent launch that takes (problem, level,
- * block of chains) units from a device-resident ready queue, so problems
- * move from level to level independently; SABR_ETIMEOUT in a result means a
- * wait of that launch gave up and its levels did not all run. */
+ * launch group (problems of one model and precision) run in one persistent
+ * launch that takes (problem, level, block of chains) units from a
+ * device-resident ready queue when the group holds several problems with
+ * more units per level than the GPU holds resident blocks, or one problem
+ * two of whose levels fit in them; problems then move from level to level
+ * independently, and SABR_ETIMEOUT in a result means a wait of that launch
+ * gave up and its levels did not all run.  Other groups launch one kernel
+ * per level.  The launch shape never changes the results. */
 sabr_status sabr_plan_stats(sabr_plan* plan, int64_t* launches_per_run,
                             double* level_kernel_ms);
 void sabr_plan_destroy(sabr_plan* plan);
