@@ -241,7 +241,7 @@ __global__ void sa_init_kernel(const ProblemDev* __restrict__ probs, const int* 
 // counters, block minima) is read from L2 (ld.global.cg), never from a
 // possibly stale L1 line.  `q` (plans only) receives the units of the next
 // level when this block closes level `level` of problem `pid`.
-template <class R, int MODEL, int PAIRS = 2>
+template <class R, int MODEL, int PAIRS = 2, bool SEL = false>
 __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int pid, int blk, int level, unsigned char* smem,
                                                const LevelQueue* q) {
   unsigned char* rest;
@@ -376,7 +376,29 @@ __device__ __forceinline__ void sa_level_block(const ProblemDev& P, int pid, int
             bool go = true;
 #pragma unroll
             for (int k = 0; k < SD; ++k) {
-              if (go && st + k < P.chain_len) {
+              if constexpr (sizeof(R) == 4 && SEL) {
+                // FP32, SEL: the decisions as selects (as in the one-step
+                // loop), so that the chains of a warp, whose steps accept and
+                // reject at different points, run the same instructions
+                const bool take = go && st + k < P.chain_len;
+                adv = take ? k + 1 : adv;
+                const bool eval = take && in[k];
+                ev += eval ? 1u : 0u;
+                const bool better = eval && cost_less(f[k], bf);
+                const float dk = cost_delta(f[k], fcur);
+                const float pacc = ex2_approx(-dk * inv_Tk);
+                const bool acc = eval && (dk <= 0.0f || u[k][D] < pacc);
+                bf = better ? f[k] : bf;
+                if (better && lane == 0) {
+#pragma unroll
+                  for (int i = 0; i < D; ++i) cbx[i] = xs[k][i];
+                }
+#pragma unroll
+                for (int i = 0; i < D; ++i) x[i] = acc ? xs[k][i] : x[i];
+                fcur = acc ? f[k] : fcur;
+                ac += acc ? 1u : 0u;
+                go = acc;
+              } else if (go && st + k < P.chain_len) {
                 adv = k + 1;
                 bool acc = false;
                 if (in[k]) {
@@ -657,7 +679,7 @@ __global__ void __launch_bounds__(kSaBlock, (LevelMinBlocks<R, MODEL>::value))
     const int4 it = work[w];
     const int lv = level >= 0 ? level : it.z;
     load_problem(probs, it.x, &P);
-    if (lv < P.n_levels) sa_level_block<R, MODEL>(P, it.x, it.y, lv, smem, nullptr);
+    if (lv < P.n_levels) sa_level_block<R, MODEL, 2, true>(P, it.x, it.y, lv, smem, nullptr);
     __syncthreads();
   }
 }
@@ -679,7 +701,11 @@ template <class R, int MODEL> struct QueuePairs {
   static constexpr int value = 5;
 };
 
-template <class R, int MODEL>
+// SEL: the speculative Hagan loop takes its decisions as selects (the
+// launches of single problems, whose chains have several lanes; in the
+// kernel that also runs the one-lane step loop of large batches they
+// measured 1.6% slower there, from its register allocation).
+template <class R, int MODEL, bool SEL = false>
 __global__ void __launch_bounds__(kLevelBlock, (QueueBlocks<R, MODEL>::value))
     sa_queue_kernel(const ProblemDev* __restrict__ probs, LevelQueue q) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -701,7 +727,7 @@ __global__ void __launch_bounds__(kLevelBlock, (QueueBlocks<R, MODEL>::value))
     const int lv = (int)((e >> 23) & (kQueueMaxLevels - 1));
     const int blk = (int)(e & (kQueueMaxBlocks - 1));
     load_problem(probs, pid, &P);
-    sa_level_block<R, MODEL, QueuePairs<R, MODEL>::value>(P, pid, blk, lv, smem, &q);
+    sa_level_block<R, MODEL, QueuePairs<R, MODEL>::value, SEL>(P, pid, blk, lv, smem, &q);
     __syncthreads();
   }
 }
@@ -1193,13 +1219,26 @@ void launch_finalize(int prec, int model, const ProblemDev* probs, const int* pl
   SABR_DISPATCH(prec, model, (sa_finalize_kernel<R, M><<<n, kSaBlock, 0, s>>>(probs, plist, queue_err)));
 }
 
+// single: the group is one problem (FP32 Hagan then takes the SEL kernel)
+static bool queue_sel(int prec, int model, bool single) { return single && prec == SABR_FP32 && model == SABR_HAGAN; }
+
 static void launch_queue(int prec, int model, const ProblemDev* probs, const LevelQueue& q, int grid, size_t smem,
-                         cudaStream_t s) {
+                         bool single, cudaStream_t s) {
+  if (queue_sel(prec, model, single)) {
+    sa_queue_kernel<float, SABR_HAGAN, true><<<grid, kLevelBlock, smem, s>>>(probs, q);
+    return;
+  }
   SABR_DISPATCH(prec, model, (sa_queue_kernel<R, M><<<grid, kLevelBlock, smem, s>>>(probs, q)));
 }
 
-static int queue_blocks_per_sm(int prec, int model, size_t smem) {
+static int queue_blocks_per_sm(int prec, int model, size_t smem, bool single) {
   int nb = 1;
+  if (queue_sel(prec, model, single)) {
+    cudaFuncSetAttribute(sa_queue_kernel<float, SABR_HAGAN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sa_queue_kernel<float, SABR_HAGAN, true>, kLevelBlock, smem);
+    return nb < 1 ? 1 : nb;
+  }
   SABR_DISPATCH(prec, model, (cudaFuncSetAttribute(sa_queue_kernel<R, M>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                               cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sa_queue_kernel<R, M>, kLevelBlock,
@@ -1294,7 +1333,7 @@ static sabr_status enqueue_plan(sabr_plan* p, cudaStream_t s, bool capturing) {
     if (!g.use_queue || g.q.total == 0) continue;
     queue_reset_kernel<<<(int)std::min<unsigned long long>(1024, (g.q.total + 255) / 256), 256, 0, s>>>(
         g.q, g.d_level0, g.n0);
-    launch_queue(g.prec, g.model, p->d_probs, g.q, g.queue_grid, g.smem_level, s);
+    launch_queue(g.prec, g.model, p->d_probs, g.q, g.queue_grid, g.smem_level, g.problems.size() == 1, s);
     launches += 2;
     ++level_launches;
   }
@@ -1435,7 +1474,8 @@ static sabr_status build_plan(int32_t n, const sabr_problem* problems, const sab
     // instead of after a kernel launch (a level's fixed cost on one smile of
     // 64 chains: 13.7 us with a launch per level); larger single problems
     // run level by level.
-    const int per_sm = std::min(workers_per_sm(g.prec, g.model), queue_blocks_per_sm(g.prec, g.model, g.smem_level));
+    const int per_sm = std::min(workers_per_sm(g.prec, g.model),
+                                queue_blocks_per_sm(g.prec, g.model, g.smem_level, g.problems.size() == 1));
     int grid = std::max(1, std::min(g.total_blocks, sms * per_sm));
     const bool single_small = g.problems.size() == 1 && 2 * g.total_blocks <= sms * per_sm && p->max_levels > 1;
     if (single_small) grid = 2 * g.total_blocks;
