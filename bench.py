@@ -152,6 +152,9 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-loads", type=float, nargs="*", default=[0.5, 0.8, 0.95],
                     help="fractions of capacity for --serve-only (each with --serve-requests requests)")
+    ap.add_argument("--serve-capacity", type=float, default=None,
+                    help="for --serve-only: the capacity (calibrations/s) the loads are fractions of, from an "
+                         "earlier run at the same request count, instead of measuring it again")
     ap.add_argument("--serve-only", action="store_true",
                     help="only the serving measurement (capacity and loads) at --serve-requests requests")
     return ap.parse_args()
@@ -680,11 +683,13 @@ def measure_fp64_one_per_launch(sg, n_per_class=6):
             "sample": "%d requests per class from the serving stream; MC scaled from 1 level x 2 proposals"
                       % n_per_class}
 
-def measure_serving_loads(sg, n_requests, fractions=(0.5, 0.8, 0.95), load_requests=None):
-    """Capacity (all requests at once), then Poisson arrivals at the given
-    fractions of it (half the requests each unless load_requests is given);
-    beside it the plain FP64 one-request-per-launch form on the same mix."""
-    burst = measure_serving(sg, n_requests, rate_hz=1e9)
+def measure_serving_loads(sg, n_requests, fractions=(0.5, 0.8, 0.95), load_requests=None, capacity=None):
+    """Capacity (all requests at once; or `capacity` from an earlier run),
+    then Poisson arrivals at the given fractions of it (half the requests
+    each unless load_requests is given); beside it the plain FP64
+    one-request-per-launch form on the same mix."""
+    burst = measure_serving(sg, n_requests, rate_hz=1e9) if capacity is None else {
+        "calibrations_per_s": capacity, "given": "from an earlier run at %d requests" % n_requests}
     cap = burst["calibrations_per_s"]
     n_load = load_requests or max(1, n_requests // 2)
     loads = {"load%d" % int(100 * f): measure_serving(sg, n_load, rate_hz=f * cap) for f in fractions}
@@ -963,7 +968,7 @@ def run_serving_only(args):
     import paper_2407_20713_gb300 as sg
     torch.cuda.set_device(0)
     out = measure_serving_loads(sg, args.serve_requests, fractions=tuple(args.serve_loads),
-                                load_requests=args.serve_requests)
+                                load_requests=args.serve_requests, capacity=args.serve_capacity)
     print(json.dumps({"serving": out, "requests": args.serve_requests}), flush=True)
 
 

@@ -166,6 +166,13 @@ def test_ready_queue_equals_level_by_level_launches(monkeypatch):
     pbs += [sg.CalibrationProblem(model=sg.HAGAN, T=np.ones(n), K=K21[:n], market=m21[:n], lo=LO4, hi=HI4,
                                   prec=sg.FP32, n_chains=20000, n_levels=6, chain_len=20, seed=35 + n)
             for n in (21, 20)]
+    # and several maturities (22 and 23 quotes): the same loops without the
+    # one-maturity numerator
+    for Tm in (np.repeat([0.5, 2.0], 11), np.concatenate([np.repeat([0.5, 2.0], 8), np.full(7, 3.0)])):
+        Km = np.tile(np.linspace(0.6, 1.4, 11), 3)[:len(Tm)]
+        pbs.append(sg.CalibrationProblem(model=sg.HAGAN, T=Tm, K=Km, market=market(T=Tm, K=Km, seed=6), lo=LO4,
+                                         hi=HI4, prec=sg.FP32, n_chains=20000, n_levels=6, chain_len=20,
+                                         seed=60 + len(Tm)))
     plan = sg.Plan(pbs, use_graph=True)
     plan.run()
     queued = plan.results()
